@@ -1,0 +1,164 @@
+"""CPU oracle for k-mer analysis (HipMer, arXiv 1705.11147, Sections 2 and 5.1).
+
+TEST INFRASTRUCTURE: only the tests, `__graft_entry__.smoke()` and the benchmark's
+`cpu_baseline` / reference leg may import this package. The product library never does.
+The computation lives in kmer_oracle.cpp (plain C++ on character strings, no Bloom filter);
+this module only marshals numpy arrays.
+
+Result layout (shared with the CUDA path's host copy, sorted by key here):
+  keys   uint64[n, 2]  (lo, hi) words of the 2-bit key, A0 C1 G2 T3, first base most significant
+  counts uint32[n]
+  ext    uint32[n, 8]  left A C G T, right A C G T
+  codes  uint8[n, 2]   left, right: 0..3 = A C G T, 4 = X (none), 5 = F (fork)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+CODE_X = 4
+CODE_F = 5
+
+_LIB = None
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("min_depth", ctypes.c_uint32),
+                ("min_ext_count", ctypes.c_uint32), ("qual_threshold", ctypes.c_uint32),
+                ("qual_offset", ctypes.c_uint32), ("canonical", ctypes.c_uint32)]
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        lib = ctypes.CDLL(_build.build())
+        p, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+        lib.oracle_run.argtypes = [p, p, p, u64, ctypes.POINTER(_Params), u32, u32, ctypes.c_int]
+        lib.oracle_run.restype = p
+        lib.oracle_size.argtypes = [p]
+        lib.oracle_size.restype = u64
+        lib.oracle_valid_windows.argtypes = [p]
+        lib.oracle_valid_windows.restype = u64
+        lib.oracle_fetch.argtypes = [p, p, p, p, p]
+        lib.oracle_query.argtypes = [p, p, u64, p, p, p]
+        lib.oracle_free.argtypes = [p]
+        lib.oracle_partition_of.argtypes = [p, u64, u32, u32, p]
+        lib.oracle_pack_strings.argtypes = [ctypes.c_char_p, u64, u32, p]
+        lib.oracle_unpack_keys.argtypes = [p, u64, u32, p]
+        _LIB = lib
+    return _LIB
+
+
+@dataclass
+class OracleResult:
+    keys: np.ndarray
+    counts: np.ndarray
+    ext: np.ndarray
+    codes: np.ndarray
+    valid_windows: int
+    _handle: object = None
+
+    def __len__(self):
+        return int(self.counts.shape[0])
+
+    def uu_mask(self) -> np.ndarray:
+        return (self.codes[:, 0] < 4) & (self.codes[:, 1] < 4)
+
+    def query(self, qkeys: np.ndarray):
+        """Look up k-mers (uint64[n, 2], either orientation) in the full counted table."""
+        if self._handle is None:
+            raise RuntimeError("result was created with keep_table=False")
+        q = np.ascontiguousarray(qkeys, dtype=np.uint64).reshape(-1, 2)
+        n = q.shape[0]
+        counts = np.zeros(n, np.uint32)
+        ext = np.zeros((n, 8), np.uint32)
+        codes = np.zeros((n, 2), np.uint8)
+        _lib().oracle_query(self._handle.ptr, q.ctypes.data, n, counts.ctypes.data,
+                            ext.ctypes.data, codes.ctypes.data)
+        return counts, ext, codes
+
+
+class _Handle:
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        if self.ptr and _LIB is not None:
+            _LIB.oracle_free(self.ptr)
+            self.ptr = None
+
+
+def run(seq: np.ndarray, qual: np.ndarray, offsets: np.ndarray, k: int, min_depth: int = 2,
+        min_ext_count: int = 2, qual_threshold: int = 20, qual_offset: int = 33,
+        canonical: bool = True, part: int = 0, n_parts: int = 1, threads: int | None = None,
+        keep_table: bool = False) -> OracleResult:
+    seq = np.ascontiguousarray(seq, dtype=np.uint8)
+    qual = np.ascontiguousarray(qual, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    n_reads = offsets.shape[0] - 1
+    prm = _Params(k, min_depth, min_ext_count, qual_threshold, qual_offset, int(bool(canonical)))
+    threads = threads or min(16, os.cpu_count() or 1)
+    lib = _lib()
+    h = lib.oracle_run(seq.ctypes.data, qual.ctypes.data, offsets.ctypes.data, n_reads,
+                       ctypes.byref(prm), part, n_parts, threads)
+    handle = _Handle(h)
+    n = lib.oracle_size(h)
+    keys = np.zeros((n, 2), np.uint64)
+    counts = np.zeros(n, np.uint32)
+    ext = np.zeros((n, 8), np.uint32)
+    codes = np.zeros((n, 2), np.uint8)
+    lib.oracle_fetch(h, keys.ctypes.data, counts.ctypes.data, ext.ctypes.data, codes.ctypes.data)
+    vw = int(lib.oracle_valid_windows(h))
+    return OracleResult(keys, counts, ext, codes, vw, handle if keep_table else None)
+
+
+def run_readset(rs, threads: int | None = None, part: int = 0, n_parts: int = 1,
+                keep_table: bool = False, **overrides) -> OracleResult:
+    p = dict(rs.meta.get("params", {}))
+    p.pop("bloom_fpr", None)
+    p.update(overrides)
+    return run(rs.seq, rs.qual, rs.offsets, threads=threads, part=part, n_parts=n_parts,
+               keep_table=keep_table, **p)
+
+
+def partition_of(keys: np.ndarray, k: int, n_parts: int) -> np.ndarray:
+    q = np.ascontiguousarray(keys, dtype=np.uint64).reshape(-1, 2)
+    out = np.zeros(q.shape[0], np.uint32)
+    _lib().oracle_partition_of(q.ctypes.data, q.shape[0], k, n_parts, out.ctypes.data)
+    return out
+
+
+def pack(kmers: list[str]) -> np.ndarray:
+    """k-mer strings (ACGT, equal length) -> uint64[n, 2] keys."""
+    if not kmers:
+        return np.zeros((0, 2), np.uint64)
+    k = len(kmers[0])
+    assert all(len(s) == k for s in kmers)
+    out = np.zeros((len(kmers), 2), np.uint64)
+    _lib().oracle_pack_strings("".join(kmers).encode(), len(kmers), k, out.ctypes.data)
+    return out
+
+
+def unpack(keys: np.ndarray, k: int) -> list[str]:
+    q = np.ascontiguousarray(keys, dtype=np.uint64).reshape(-1, 2)
+    buf = ctypes.create_string_buffer(q.shape[0] * k + 1)
+    _lib().oracle_unpack_keys(q.ctypes.data, q.shape[0], k, buf)
+    raw = buf.raw[: q.shape[0] * k].decode()
+    return [raw[i * k:(i + 1) * k] for i in range(q.shape[0])]
+
+
+def reads_from_strings(reads: list[str], quals: list[str] | None = None, default_q: int = 40):
+    """Build (seq, qual, offsets) arrays from Python strings (qualities Phred+33)."""
+    seq = np.frombuffer("".join(reads).encode(), dtype=np.uint8).copy()
+    if quals is None:
+        qual = np.full(seq.shape[0], 33 + default_q, np.uint8)
+    else:
+        qual = np.frombuffer("".join(quals).encode(), dtype=np.uint8).copy()
+    offs = np.zeros(len(reads) + 1, np.uint64)
+    offs[1:] = np.cumsum([len(r) for r in reads])
+    return seq, qual, offs

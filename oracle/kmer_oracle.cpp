@@ -1,0 +1,307 @@
+// Plain CPU oracle for the k-mer analysis stage of HipMer (arXiv 1705.11147, Sections 2 and 5.1).
+//
+// TEST INFRASTRUCTURE ONLY. Nothing in the product library may include, link or call this
+// file; only the tests, the package's smoke check and the benchmark's CPU-baseline leg use it.
+// It shares no code with the CUDA path: it works on character strings, uses std::unordered_map
+// and has no Bloom filter (the Bloom filter may never change the result, Section 5.1).
+//
+// What it computes, step by step in the paper's terms:
+//  1. Chopping (Section 2, item 1; Fig. "combined"(b)): every read of length L yields the
+//     L-k+1 overlapping substrings of length k ("windows"). A window is kept only if all of
+//     its k characters are A, C, G or T after case folding (the paper does not say how N or
+//     other symbols are treated; reading: they invalidate every window that covers them).
+//  2. Canonical form (not stated in the paper; reverse complements are named in Section 7):
+//     the key of a window w is the lexicographically smaller of w and its reverse complement,
+//     with A < C < G < T. With canonical = 0 the key is w itself (the paper's k = 3 figures).
+//  3. Counting (Section 5.1): count[key] += 1 for every window.
+//  4. Extensions (Section 5.1: two arrays of four counters per k-mer, one per end): the base
+//     before the window and the base after it are each counted if they exist, are ACGT and
+//     have Phred quality >= qual_threshold. When the key is the reverse complement of w, the
+//     sides swap and the bases are complemented.
+//  5. Error filter (Section 2 item 1, Section 5.1): keep keys with count >= min_depth
+//     (the paper keeps k-mers occurring "more than epsilon" times: min_depth = epsilon + 1).
+//  6. High-quality extensions (Section 5.1, threshold t_hq): on each side the set
+//     H = {b : ext[b] >= min_ext_count}. The side code is b if |H| = 1, X (no neighbour,
+//     Section 4.1) if |H| = 0 and F (fork, excluded from contigs, Section 2) if |H| >= 2.
+//     Unique-extension (UU, Section 5.2) k-mers have A/C/G/T on both sides.
+//  7. Owner-computes partitioning (Section 5.1, "necessary and sufficient"): with n_parts > 1
+//     only keys with fnv1a(key string) mod n_parts == part are kept; the union over all parts
+//     equals the whole result. The FNV-1a hash here is the oracle's own.
+//
+// Output: records sorted by key; key = 2-bit codes A0 C1 G2 T3, first base most
+// significant, as a 128-bit number split into (lo, hi) 64-bit words.
+
+#include <algorithm>
+#include <array>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+struct Params {
+  uint32_t k;
+  uint32_t min_depth;
+  uint32_t min_ext_count;
+  uint32_t qual_threshold;
+  uint32_t qual_offset;
+  uint32_t canonical;
+};
+
+struct Rec {
+  uint32_t count = 0;
+  uint32_t ext[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // left A C G T, right A C G T
+};
+
+using Key = std::array<uint64_t, 2>;  // (lo, hi)
+
+struct KeyHash {
+  size_t operator()(const Key& k) const {
+    uint64_t h = k[0] * 0x9E3779B97F4A7C15ull ^ (k[1] + 0x632BE59BD9B4E019ull + (k[0] >> 17));
+    return (size_t)(h ^ (h >> 29));
+  }
+};
+
+using Map = std::unordered_map<Key, Rec, KeyHash>;
+
+char fold(uint8_t c) { return (c >= 'a' && c <= 'z') ? (char)(c - 'a' + 'A') : (char)c; }
+
+bool is_acgt(char c) { return c == 'A' || c == 'C' || c == 'G' || c == 'T'; }
+
+int code_of(char c) {
+  switch (c) {
+    case 'A': return 0;
+    case 'C': return 1;
+    case 'G': return 2;
+    default: return 3;  // 'T'
+  }
+}
+
+char complement(char c) {
+  switch (c) {
+    case 'A': return 'T';
+    case 'C': return 'G';
+    case 'G': return 'C';
+    default: return 'A';  // 'T'
+  }
+}
+
+std::string reverse_complement(const std::string& w) {
+  std::string r(w.rbegin(), w.rend());
+  for (char& c : r) c = complement(c);
+  return r;
+}
+
+Key pack(const std::string& key) {
+  unsigned __int128 v = 0;
+  for (char c : key) v = (v << 2) | (unsigned __int128)code_of(c);
+  return Key{(uint64_t)v, (uint64_t)(v >> 64)};
+}
+
+std::string unpack(const Key& key, uint32_t k) {
+  unsigned __int128 v = ((unsigned __int128)key[1] << 64) | key[0];
+  std::string s(k, 'A');
+  for (uint32_t i = 0; i < k; ++i) s[k - 1 - i] = "ACGT"[(int)(v & 3)], v >>= 2;
+  return s;
+}
+
+uint64_t fnv1a(const std::string& s) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (char c : s) h = (h ^ (uint8_t)c) * 0x100000001b3ull;
+  return h;
+}
+
+bool usable(const std::string& s, const uint8_t* q, int64_t j, const Params& p) {
+  if (j < 0 || j >= (int64_t)s.size()) return false;
+  if (!is_acgt(s[(size_t)j])) return false;
+  return (int)q[j] - (int)p.qual_offset >= (int)p.qual_threshold;
+}
+
+// Steps 1-4 over reads [r0, r1) into map m; returns the number of valid windows seen
+// (before partition filtering).
+uint64_t count_reads(const uint8_t* seq, const uint8_t* qual, const uint64_t* offsets,
+                     uint64_t r0, uint64_t r1, const Params& p, uint32_t part,
+                     uint32_t n_parts, Map& m) {
+  uint64_t valid_windows = 0;
+  const int64_t k = p.k;
+  for (uint64_t r = r0; r < r1; ++r) {
+    const int64_t L = (int64_t)(offsets[r + 1] - offsets[r]);
+    const uint8_t* q = qual + offsets[r];
+    std::string s(L, ' ');
+    for (int64_t j = 0; j < L; ++j) s[(size_t)j] = fold(seq[offsets[r] + j]);
+    for (int64_t i = 0; i + k <= L; ++i) {
+      std::string w = s.substr((size_t)i, (size_t)k);
+      if (!std::all_of(w.begin(), w.end(), is_acgt)) continue;
+      ++valid_windows;
+      std::string rc = reverse_complement(w);
+      const bool forward = !p.canonical || w <= rc;
+      const std::string& key = forward ? w : rc;
+      if (n_parts > 1 && fnv1a(key) % n_parts != part) continue;
+      Rec& rec = m[pack(key)];
+      rec.count += 1;
+      const bool left_ok = usable(s, q, i - 1, p);
+      const bool right_ok = usable(s, q, i + k, p);
+      if (forward) {
+        if (left_ok) rec.ext[0 + code_of(s[(size_t)(i - 1)])] += 1;
+        if (right_ok) rec.ext[4 + code_of(s[(size_t)(i + k)])] += 1;
+      } else {
+        // Reverse-complement orientation: the base after w precedes the key (complemented),
+        // the base before w follows it (complemented).
+        if (right_ok) rec.ext[0 + code_of(complement(s[(size_t)(i + k)]))] += 1;
+        if (left_ok) rec.ext[4 + code_of(complement(s[(size_t)(i - 1)]))] += 1;
+      }
+    }
+  }
+  return valid_windows;
+}
+
+uint8_t side_code(const uint32_t* e, uint32_t min_ext) {
+  int n = 0, b = 0;
+  for (int j = 0; j < 4; ++j)
+    if (e[j] >= min_ext) ++n, b = j;
+  if (n == 0) return 4;  // X
+  if (n >= 2) return 5;  // F
+  return (uint8_t)b;
+}
+
+struct Result {
+  Params p;
+  uint64_t valid_windows = 0;
+  std::vector<Key> keys;
+  std::vector<Rec> recs;
+  Map table;  // all counted keys (before the min_depth filter), kept for queries
+};
+
+}  // namespace
+
+extern "C" {
+
+typedef struct {
+  uint32_t k, min_depth, min_ext_count, qual_threshold, qual_offset, canonical;
+} oracle_params;
+
+void* oracle_run(const uint8_t* seq, const uint8_t* qual, const uint64_t* offsets,
+                 uint64_t n_reads, const oracle_params* op, uint32_t part, uint32_t n_parts,
+                 int n_threads) {
+  Params p{op->k, op->min_depth, op->min_ext_count, op->qual_threshold, op->qual_offset,
+           op->canonical};
+  if (n_parts == 0) n_parts = 1;
+  if (n_threads < 1) n_threads = 1;
+  if ((uint64_t)n_threads > n_reads) n_threads = n_reads ? (int)n_reads : 1;
+  std::vector<Map> maps((size_t)n_threads);
+  std::vector<uint64_t> windows((size_t)n_threads, 0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < n_threads; ++t) {
+    uint64_t r0 = n_reads * (uint64_t)t / (uint64_t)n_threads;
+    uint64_t r1 = n_reads * (uint64_t)(t + 1) / (uint64_t)n_threads;
+    th.emplace_back([&, t, r0, r1] {
+      windows[(size_t)t] = count_reads(seq, qual, offsets, r0, r1, p, part, n_parts, maps[(size_t)t]);
+    });
+  }
+  for (auto& x : th) x.join();
+  Result* res = new Result();
+  res->p = p;
+  Map& all = res->table;
+  all = std::move(maps[0]);
+  res->valid_windows = windows[0];
+  for (size_t t = 1; t < maps.size(); ++t) {
+    res->valid_windows += windows[t];
+    for (auto& kv : maps[t]) {
+      Rec& r = all[kv.first];
+      r.count += kv.second.count;
+      for (int j = 0; j < 8; ++j) r.ext[j] += kv.second.ext[j];
+    }
+    Map().swap(maps[t]);
+  }
+  std::vector<std::pair<Key, Rec>> kept;
+  for (auto& kv : all)
+    if (kv.second.count >= p.min_depth) kept.push_back(kv);
+  std::sort(kept.begin(), kept.end(), [](const std::pair<Key, Rec>& a, const std::pair<Key, Rec>& b) {
+    return a.first[1] != b.first[1] ? a.first[1] < b.first[1] : a.first[0] < b.first[0];
+  });
+  res->keys.reserve(kept.size());
+  res->recs.reserve(kept.size());
+  for (auto& kv : kept) res->keys.push_back(kv.first), res->recs.push_back(kv.second);
+  return res;
+}
+
+uint64_t oracle_size(void* h) { return ((Result*)h)->keys.size(); }
+
+uint64_t oracle_valid_windows(void* h) { return ((Result*)h)->valid_windows; }
+
+void oracle_fetch(void* h, uint64_t* keys, uint32_t* counts, uint32_t* ext, uint8_t* codes) {
+  Result* r = (Result*)h;
+  for (size_t i = 0; i < r->keys.size(); ++i) {
+    keys[2 * i] = r->keys[i][0];
+    keys[2 * i + 1] = r->keys[i][1];
+    counts[i] = r->recs[i].count;
+    std::memcpy(ext + 8 * i, r->recs[i].ext, sizeof(uint32_t) * 8);
+    codes[2 * i] = side_code(r->recs[i].ext, r->p.min_ext_count);
+    codes[2 * i + 1] = side_code(r->recs[i].ext + 4, r->p.min_ext_count);
+  }
+}
+
+// Lookup (the read-only phase, Section 4.2 use case GRO). A query k-mer may be given in
+// either orientation; the answer is expressed in the query's own orientation. Keys below
+// min_depth (or absent) answer count 0, zero extensions and codes X/X.
+void oracle_query(void* h, const uint64_t* qkeys, uint64_t n, uint32_t* counts, uint32_t* ext,
+                  uint8_t* codes) {
+  Result* r = (Result*)h;
+  const Params& p = r->p;
+  for (uint64_t i = 0; i < n; ++i) {
+    std::string w = unpack(Key{qkeys[2 * i], qkeys[2 * i + 1]}, p.k);
+    std::string rc = reverse_complement(w);
+    const bool forward = !p.canonical || w <= rc;
+    auto it = r->table.find(pack(forward ? w : rc));
+    uint32_t e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t c = 0;
+    if (it != r->table.end() && it->second.count >= p.min_depth) {
+      c = it->second.count;
+      for (int b = 0; b < 4; ++b) {
+        if (forward) {
+          e[b] = it->second.ext[b];
+          e[4 + b] = it->second.ext[4 + b];
+        } else {
+          // the query's left neighbours are the complements of the key's right neighbours
+          e[code_of(complement("ACGT"[b]))] = it->second.ext[4 + b];
+          e[4 + code_of(complement("ACGT"[b]))] = it->second.ext[b];
+        }
+      }
+    }
+    counts[i] = c;
+    std::memcpy(ext + 8 * i, e, sizeof(e));
+    codes[2 * i] = c ? side_code(e, p.min_ext_count) : 4;
+    codes[2 * i + 1] = c ? side_code(e + 4, p.min_ext_count) : 4;
+  }
+}
+
+void oracle_free(void* h) { delete (Result*)h; }
+
+// The oracle's owner map (step 7): partition id of each packed key.
+void oracle_partition_of(const uint64_t* keys, uint64_t n, uint32_t k, uint32_t n_parts,
+                         uint32_t* out) {
+  for (uint64_t i = 0; i < n; ++i)
+    out[i] = (uint32_t)(fnv1a(unpack(Key{keys[2 * i], keys[2 * i + 1]}, k)) % n_parts);
+}
+
+// 2-bit packing of k-mer strings (ACGT only, length k each, concatenated), as the oracle
+// packs keys; lets tests state inputs and expected keys as text.
+void oracle_pack_strings(const char* s, uint64_t n, uint32_t k, uint64_t* keys) {
+  for (uint64_t i = 0; i < n; ++i) {
+    Key key = pack(std::string(s + i * k, k));
+    keys[2 * i] = key[0];
+    keys[2 * i + 1] = key[1];
+  }
+}
+
+void oracle_unpack_keys(const uint64_t* keys, uint64_t n, uint32_t k, char* out) {
+  for (uint64_t i = 0; i < n; ++i) {
+    std::string s = unpack(Key{keys[2 * i], keys[2 * i + 1]}, k);
+    std::memcpy(out + i * k, s.data(), k);
+  }
+}
+
+}  // extern "C"

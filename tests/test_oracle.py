@@ -1,0 +1,287 @@
+"""Pins for the CPU oracle against what the paper and plain mathematics fix.
+
+- the paper's worked examples (Section 2 chopping figure, Section 2 fork, Section 5.2 CTG
+  entry), stored as text fixtures under tests/golden/;
+- a brute-force restatement on tiny inputs written independently here (Python strings,
+  str.translate, collections.Counter);
+- invariants: total count = valid windows, reverse-complement symmetry, read-order and
+  partition independence, extension sums;
+- a statistical check of the Section 2 coverage formula f = d (1 - (k-1)/L).
+"""
+import os
+import re
+from collections import Counter
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+CODE = {"A": 0, "C": 1, "G": 2, "T": 3, "X": 4, "F": 5}
+
+
+def _fixture(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _as_dict(res, k):
+    strs = oracle.unpack(res.keys, k)
+    return {s: (int(res.counts[i]), tuple(int(x) for x in res.ext[i]), tuple(int(x) for x in res.codes[i]))
+            for i, s in enumerate(strs)}
+
+
+# ------------------------------------------------------------------ paper worked examples
+
+def test_chopping_example_forward():
+    seq, qual, offs = oracle.reads_from_strings(["GATCTGAACCG"])
+    res = oracle.run(seq, qual, offs, k=3, min_depth=1, min_ext_count=1, canonical=False)
+    got = {s: int(c) for s, c in zip(oracle.unpack(res.keys, 3), res.counts)}
+    want = {r[0]: int(r[1]) for r in _fixture("chop_GATCTGAACCG_k3.txt")}
+    assert got == want
+    assert res.valid_windows == 9
+
+
+def test_chopping_example_canonical():
+    seq, qual, offs = oracle.reads_from_strings(["GATCTGAACCG"])
+    res = oracle.run(seq, qual, offs, k=3, min_depth=1, min_ext_count=1, canonical=True)
+    got = _as_dict(res, 3)
+    want = {}
+    for key, cnt, left, right in _fixture("canonical_GATCTGAACCG_k3.txt"):
+        want[key] = (int(cnt), tuple(int(x) for x in left.split(",")) + tuple(int(x) for x in right.split(",")))
+    assert {s: (v[0], v[1]) for s, v in got.items()} == want
+    assert int(res.counts.sum()) == 9
+
+
+def test_contig_entry_ctg():
+    seq, qual, offs = oracle.reads_from_strings(["GATCTGA", "GATCTGA"])
+    res = oracle.run(seq, qual, offs, k=3, min_depth=2, min_ext_count=2, canonical=False)
+    got = _as_dict(res, 3)
+    for kmer, left, right in _fixture("contig_CTG_value.txt"):
+        assert got[kmer][2] == (CODE[left], CODE[right]), kmer
+    # the two-letter value of CTG rendered [right][left] is "AT"
+    c = got["CTG"][2]
+    assert "ACGT"[c[1]] + "ACGT"[c[0]] == "AT"
+
+
+def test_fork_gaa():
+    seq, qual, offs = oracle.reads_from_strings(["GAAC", "GAAC", "GAAT", "GAAT"])
+    res = oracle.run(seq, qual, offs, k=3, min_depth=2, min_ext_count=2, canonical=False)
+    got = _as_dict(res, 3)
+    for kmer, cnt, left, right in _fixture("fork_GAA.txt"):
+        assert got[kmer][0] == int(cnt)
+        assert got[kmer][2] == (CODE[left], CODE[right]), kmer
+    uu = res.uu_mask()
+    assert not uu.any()  # no k-mer here has unique extensions on both sides
+
+
+def test_quality_gate_boundary():
+    seq, qual, offs = oracle.reads_from_strings(["ACGTA"], ["54II4"])
+    res = oracle.run(seq, qual, offs, k=3, min_depth=1, min_ext_count=1, canonical=False,
+                     qual_threshold=20)
+    got = _as_dict(res, 3)
+    for kmer, cnt, left, right in _fixture("quality_gate.txt"):
+        e = tuple(int(x) for x in left.split(",")) + tuple(int(x) for x in right.split(","))
+        assert got[kmer][:2] == (int(cnt), e), kmer
+
+
+# ------------------------------------------------------------------ brute force
+
+COMP = str.maketrans("ACGT", "TGCA")
+
+
+def brute_force(reads, quals, k, min_depth, min_ext, Q, qoff=33, canonical=True):
+    """Independent restatement: enumerate substrings, flip by string reversal."""
+    table = {}
+    for s, q in zip(reads, quals):
+        s = s.upper()
+        ok = [c in "ACGT" and ord(qc) - qoff >= Q for c, qc in zip(s, q)]
+        for i in range(len(s) - k + 1):
+            w = s[i:i + k]
+            if re.fullmatch("[ACGT]+", w) is None:
+                continue
+            rc = w.translate(COMP)[::-1]
+            before = s[i - 1] if i > 0 and ok[i - 1] else None
+            after = s[i + k] if i + k < len(s) and ok[i + k] else None
+            if canonical and rc < w:
+                key, left, right = rc, (after.translate(COMP) if after else None), \
+                    (before.translate(COMP) if before else None)
+            else:
+                key, left, right = w, before, after
+            rec = table.setdefault(key, [0, Counter(), Counter()])
+            rec[0] += 1
+            if left:
+                rec[1][left] += 1
+            if right:
+                rec[2][right] += 1
+    out = {}
+    for key, (cnt, lc, rc_) in table.items():
+        if cnt < min_depth:
+            continue
+        ext = tuple(lc[b] for b in "ACGT") + tuple(rc_[b] for b in "ACGT")
+
+        def code(cn):
+            hq = [b for b in "ACGT" if cn[b] >= min_ext]
+            return CODE["X"] if not hq else (CODE[hq[0]] if len(hq) == 1 else CODE["F"])
+        out[key] = (cnt, ext, (code(lc), code(rc_)))
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 7, 31, 33, 63])
+@pytest.mark.parametrize("canonical", [True, False])
+def test_brute_force_tiny(k, canonical):
+    rs = synth.random_reads(seed=1000 + k, n_reads=60, min_len=0, max_len=90,
+                            alphabet=b"ACGTACGTACGTacgtNR", q_lo=15, q_hi=25)
+    reads = [bytes(rs.seq[int(rs.offsets[i]):int(rs.offsets[i + 1])]).decode() for i in range(rs.n_reads)]
+    quals = [bytes(rs.qual[int(rs.offsets[i]):int(rs.offsets[i + 1])]).decode() for i in range(rs.n_reads)]
+    for md, me in [(1, 1), (2, 2), (3, 1)]:
+        res = oracle.run(rs.seq, rs.qual, rs.offsets, k=k, min_depth=md, min_ext_count=me,
+                         qual_threshold=20, canonical=canonical)
+        assert _as_dict(res, k) == brute_force(reads, quals, k, md, me, 20, canonical=canonical)
+
+
+def test_brute_force_low_complexity():
+    # repeats inside reads: same k-mer many times in one read, palindromic neighbourhoods
+    reads = ["ACACACACACACACACAC", "TTTTTTTTTTTT", "AAAAAAAAAAAAAAAA", "ACGTACGTACGT", "GCGCGCGC" * 3]
+    quals = ["I" * len(r) for r in reads]
+    seq, qual, offs = oracle.reads_from_strings(reads, quals)
+    for k in (3, 5, 7):
+        res = oracle.run(seq, qual, offs, k=k, min_depth=1, min_ext_count=2)
+        assert _as_dict(res, k) == brute_force(reads, quals, k, 1, 2, 20)
+
+
+# ------------------------------------------------------------------ invariants
+
+@pytest.fixture(scope="module")
+def small_set():
+    return synth.workload("bacterial_5m", scale=0.02)  # 100 kbp genome, N bases, repeats
+
+
+def _valid_windows_python(rs, k):
+    n = 0
+    for i in range(rs.n_reads):
+        s = bytes(rs.seq[int(rs.offsets[i]):int(rs.offsets[i + 1])]).decode().upper()
+        for run in re.findall("[ACGT]+", s):
+            n += max(len(run) - k + 1, 0)
+    return n
+
+
+def test_total_count_equals_valid_windows(small_set):
+    k = 51
+    res = oracle.run_readset(small_set, min_depth=1)
+    assert int(res.counts.astype(np.int64).sum()) == res.valid_windows
+    assert res.valid_windows == _valid_windows_python(small_set, k)
+
+
+def test_extension_sums_bounded(small_set):
+    res = oracle.run_readset(small_set, min_depth=1, min_ext_count=1)
+    left = res.ext[:, :4].astype(np.int64).sum(1)
+    right = res.ext[:, 4:].astype(np.int64).sum(1)
+    assert (left <= res.counts).all() and (right <= res.counts).all()
+    # every read has exactly one window without a left neighbour and one without a right
+    # neighbour (if it has a valid window at its ends), so the deficits are positive overall
+    assert left.sum() < res.counts.astype(np.int64).sum()
+
+
+def _revcomp_readset(rs):
+    comp = np.arange(256, dtype=np.uint8)
+    for a, b in zip(b"ACGTacgt", b"TGCAtgca"):
+        comp[a] = b
+    seq = np.empty_like(rs.seq)
+    qual = np.empty_like(rs.qual)
+    for i in range(rs.n_reads):
+        a, b = int(rs.offsets[i]), int(rs.offsets[i + 1])
+        seq[a:b] = comp[rs.seq[a:b][::-1]]
+        qual[a:b] = rs.qual[a:b][::-1]
+    return seq, qual
+
+
+def test_reverse_complement_invariance(small_set):
+    res = oracle.run_readset(small_set)
+    seq, qual = _revcomp_readset(small_set)
+    res2 = oracle.run(seq, qual, small_set.offsets, **_params(small_set))
+    for f in ("keys", "counts", "ext", "codes"):
+        np.testing.assert_array_equal(getattr(res, f), getattr(res2, f))
+
+
+def _params(rs):
+    p = dict(rs.meta["params"])
+    p.pop("bloom_fpr")
+    return p
+
+
+def test_read_order_invariance(small_set):
+    res = oracle.run_readset(small_set)
+    perm = np.random.default_rng(5).permutation(small_set.n_reads)
+    lens = np.diff(small_set.offsets.astype(np.int64))[perm]
+    offs = np.zeros(small_set.n_reads + 1, np.uint64)
+    offs[1:] = np.cumsum(lens)
+    seq = np.concatenate([small_set.seq[int(small_set.offsets[i]):int(small_set.offsets[i + 1])] for i in perm])
+    qual = np.concatenate([small_set.qual[int(small_set.offsets[i]):int(small_set.offsets[i + 1])] for i in perm])
+    res2 = oracle.run(seq, qual, offs, **_params(small_set))
+    for f in ("keys", "counts", "ext", "codes"):
+        np.testing.assert_array_equal(getattr(res, f), getattr(res2, f))
+
+
+def test_partition_union_equals_whole(small_set):
+    """Owner-computes (Section 5.1): the union of the per-owner results is the result."""
+    whole = oracle.run_readset(small_set)
+    parts = [oracle.run_readset(small_set, part=i, n_parts=5) for i in range(5)]
+    keys = np.concatenate([p.keys for p in parts])
+    order = np.lexsort((keys[:, 0], keys[:, 1]))
+    np.testing.assert_array_equal(keys[order], whole.keys)
+    np.testing.assert_array_equal(np.concatenate([p.counts for p in parts])[order], whole.counts)
+    np.testing.assert_array_equal(np.concatenate([p.ext for p in parts])[order], whole.ext)
+    for i, p in enumerate(parts):
+        assert (oracle.partition_of(p.keys, 51, 5) == i).all()
+
+
+def test_threads_do_not_change_result(small_set):
+    a = oracle.run_readset(small_set, threads=1)
+    b = oracle.run_readset(small_set, threads=7)
+    for f in ("keys", "counts", "ext", "codes"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
+
+
+def test_query_reorients():
+    seq, qual, offs = oracle.reads_from_strings(["GATCTGAACCG"])
+    res = oracle.run(seq, qual, offs, k=3, min_depth=1, min_ext_count=1, keep_table=True)
+    counts, ext, codes = res.query(oracle.pack(["ATC", "GAT", "TTT"]))
+    assert list(counts) == [2, 2, 0]
+    assert list(ext[0]) == [0, 0, 2, 0, 0, 0, 0, 1]      # left G x2, right T x1
+    assert list(ext[1]) == [1, 0, 0, 0, 0, 2, 0, 0]      # seen as GAT: left A x1, right C x2
+    assert list(codes[1]) == [0, 1] and list(codes[2]) == [4, 4]
+
+
+def test_pack_roundtrip():
+    kmers = ["A" * 63, "T" * 63, "ACGT" * 15 + "ACG", "C" * 31, "G"]
+    for s in kmers:
+        keys = oracle.pack([s])
+        assert oracle.unpack(keys, len(s)) == [s]
+    k = oracle.pack(["T" * 63])
+    assert int(k[0, 1]) == 2**62 - 1 and int(k[0, 0]) == 2**64 - 1
+    k = oracle.pack(["C" + "A" * 30])
+    assert int(k[0, 0]) == 1 << 60 and int(k[0, 1]) == 0
+
+
+# ------------------------------------------------------------------ statistics (Section 2)
+
+def test_coverage_formula_peak():
+    """Section 2: a true k-mer is expected f = d (1 - (k-1)/L) times; error-free occurrences
+    scale that by (1 - e)^k. The count histogram of solid keys peaks near that value."""
+    rs = synth.workload("plain_1m", scale=0.25)
+    res = oracle.run_readset(rs)
+    d, L, k, e = 30, 150, 31, 0.005
+    f = d * (1 - (k - 1) / L) * (1 - e) ** k
+    hist = np.bincount(res.counts[res.counts >= 5].astype(np.int64))
+    mode = int(np.argmax(hist))
+    assert abs(mode - f) <= 2.0, (mode, f)
+    mean = float(res.counts[res.counts >= 8].mean())
+    assert abs(mean - f) / f < 0.05, (mean, f)
