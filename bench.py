@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""k-mer analysis throughput on GB300 (HipMer k-mer analysis stage, arXiv 1705.11147 Sec. 5.1).
+
+One step = the whole hot path over the workload's reads, inputs resident in HBM:
+  reset (Bloom filter, table) -> count (pack + Bloom pass) -> finalize (recount + classify
+  and compaction) -> query (1 M present + 1 M random k-mers).
+value = valid windows (k-mer occurrences) / step time, in G k-mers/s.
+
+Default workload: the 200 Mbp genome with 5 % repeats, 30x of 250 bp reads (24 M reads,
+6 Gbases, 4.8 G windows), k = 51, Bloom pass at 1 % FPR, min depth 4, Q20. The 12 GB of
+reads are far larger than L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload large_200m|bacterial_5m|plain_1m] [--no-e2e] [--no-cpu]
+
+Under torchrun (N > 1) each rank owns 1/N of the k-mers (owner-computes, Section 5.1):
+every rank scans all reads but counts only its own keys, no data-path collective; the time
+is the max over ranks (strong scaling). --impl reference times the CPU oracle on a bounded
+sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "k-mer analysis Gk-mers/s & HBM GB/s at 1 GB300; batched vs plain, bit-exact"
+UNIT = "Gk-mers/s"
+
+
+# ------------------------------------------------------------------ sizing
+
+def workload_sizing(rs, n_parts: int = 1) -> dict:
+    """Bloom and table sizes from the read set's recipe (genome size, coverage, error rate):
+    what a user who knows the approximate genome size would pass. Results never depend on
+    these; a table that turns out too small is reported (KMA_EFULL), not truncated."""
+    m = rs.meta
+    p = m["params"]
+    k, G, e, L = p["k"], m["G"], m["err"], m["L"]
+    W = rs.windows_upper_bound(k)
+    p_err = 1.0 - (1.0 - e) ** k                 # windows holding at least one error
+    distinct = G + W * p_err                      # true k-mers + (mostly unique) error k-mers
+    f = m["coverage"] * (1.0 - (k - 1) / L)       # Section 2: expected occurrences of a k-mer
+    lam = f * (e / 3.0) * (1.0 - e) ** (k - 1)    # reads sharing one specific error k-mer
+    twice = G * k * 3 * (1.0 - math.exp(-lam) * (1.0 + lam))
+    keys = G + twice + p.get("bloom_fpr", 0.01) * W * p_err
+    return dict(expected_distinct=int(distinct * 1.05 / n_parts) + 1024,
+                expected_keys=int(keys * 1.25 / n_parts) + 1024)
+
+
+def make_handle_params(rs, n_parts=1, part=0, **tuning):
+    from paper_1705_11147_gb300 import make_params
+    p = rs.meta["params"]
+    size = workload_sizing(rs, n_parts)
+    return make_params(k=p["k"], min_depth=p["min_depth"], min_ext_count=2,
+                       qual_threshold=p["qual_threshold"], use_bloom=True,
+                       bloom_fpr=p.get("bloom_fpr", 0.01), max_bases=rs.n_bases,
+                       max_reads=rs.n_reads, n_parts=n_parts, part=part, **size, **tuning)
+
+
+def run_large_once(rs, **tuning):
+    """The bench's launch configuration, once, result copied to the host (used by the
+    full-size sampled parity test)."""
+    import torch
+    from paper_1705_11147_gb300 import KmerAnalysis
+    seq = torch.from_numpy(rs.seq).cuda()
+    qual = torch.from_numpy(rs.qual).cuda()
+    offs = torch.from_numpy(rs.offsets.astype(np.int64)).cuda()
+    with KmerAnalysis(make_handle_params(rs, **tuning)) as ka:
+        ka.count(seq, qual, offs)
+        ka.finalize()
+        res = ka.copy_result()
+    del seq, qual, offs
+    torch.cuda.empty_cache()
+    return res
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """Barrier + max of a per-rank time (the only cross-rank operation: timing, not data)."""
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+
+def cpu_baseline(rs, budget_s: float = 15.0, threads: int | None = None) -> dict:
+    """The oracle as it stands, timed on a prefix of the workload's reads sized for about
+    `budget_s` seconds of CPU work on all host cores."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    k = rs.meta["params"]["k"]
+
+    def prefix(n):
+        n = min(n, rs.n_reads)
+        offs = rs.offsets[: n + 1]
+        return rs.seq[: int(offs[-1])], rs.qual[: int(offs[-1])], offs
+
+    p = dict(rs.meta["params"])
+    p.pop("bloom_fpr", None)
+    n = 20000
+    s, q, o = prefix(n)
+    t0 = time.perf_counter()
+    r = oracle.run(s, q, o, threads=threads, **p)
+    dt = time.perf_counter() - t0
+    rate = r.valid_windows / max(dt, 1e-9)
+    n = int(min(rs.n_reads, max(n, n * budget_s / max(dt, 1e-6))))
+    s, q, o = prefix(n)
+    t0 = time.perf_counter()
+    r = oracle.run(s, q, o, threads=threads, **p)
+    dt = time.perf_counter() - t0
+    return {"value": r.valid_windows / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n} of {rs.n_reads} reads ({r.valid_windows} windows, k={k}), "
+                      f"{dt:.1f} s wall on {threads} threads",
+            "seconds": dt, "windows": int(r.valid_windows), "reads": n,
+            "calibration_rate": rate / 1e9}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def roofline(timing: dict, res_info, positions: int, peak_gbs: float, steps: int) -> dict:
+    """Dominant kernel: the first pass (Bloom test-and-set + table insert/update).
+    Algorithmic bytes per launch, 32-byte sectors, Bloom filter and table far larger than L2:
+      64 B per valid window  (Bloom word: sector read + write-back)
+     128 B per window whose k-mer the filter had seen (slot: key/count sector and extension
+           sector, each read + written back)
+     0.625 B per arena position (2-bit codes, invalid and quality bits read, marks written)."""
+    W = int(res_info.valid_windows)
+    F = int(timing["first_sightings"])
+    seen = W - F
+    algo_bytes = 64.0 * W + 128.0 * seen + 0.625 * positions
+    ms = timing["ms_pass"] / max(timing["n_pass"], 1)
+    achieved = algo_bytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs, "unit": "GB/s",
+            "frac": round(achieved / peak_gbs, 4), "traffic": None,
+            "kernel": "pass_kernel (Bloom mode)", "ms_per_launch": round(ms, 3),
+            "algo_bytes_per_launch": int(algo_bytes), "peak_source": "of measured (hbm_gbs)"}
+
+
+def load_peak() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # fallback figure of the profiling recipe
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_1705_11147_gb300 import KmerAnalysis
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    t_gen = time.perf_counter()
+    rs = synth.workload(args.workload, scale=args.scale)
+    t_gen = time.perf_counter() - t_gen
+    k = rs.meta["params"]["k"]
+    seq = torch.from_numpy(rs.seq).to(dev)
+    qual = torch.from_numpy(rs.qual).to(dev)
+    offs = torch.from_numpy(rs.offsets.astype(np.int64)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    prm = make_handle_params(rs, n_parts=ws, part=rank)
+    ka = KmerAnalysis(prm, stream=stream)
+
+    # query set: 1 M k-mers present in the result + 1 M random k-mers (mostly absent)
+    ka.count(seq, qual, offs)
+    info = ka.finalize()
+    n_res = int(info.n)
+    keys_dev, _, _, _ = ka.copy_result_device()
+    g = torch.Generator(device=dev).manual_seed(1234 + rank)
+    nq = min(args.queries, max(n_res, 1))
+    pick = torch.randint(0, max(n_res, 1), (nq,), device=dev, generator=g)
+    present = keys_dev[pick] if n_res else torch.zeros((0, 2), dtype=torch.int64, device=dev)
+    rnd = torch.randint(0, 2**62, (args.queries, 2), device=dev, generator=g, dtype=torch.int64)
+    rnd[:, 1] &= (1 << max(2 * k - 64, 0)) - 1 if 2 * k > 64 else 0
+    if 2 * k <= 64:
+        rnd[:, 0] &= (1 << (2 * k)) - 1
+    qkeys = torch.cat([present, rnd]).contiguous()
+    del keys_dev
+    q_out = (torch.empty(qkeys.shape[0], dtype=torch.int32, device=dev),
+             torch.empty((qkeys.shape[0], 8), dtype=torch.int32, device=dev),
+             torch.empty((qkeys.shape[0], 2), dtype=torch.uint8, device=dev))
+
+    def step():
+        ka.reset()
+        ka.count(seq, qual, offs)
+        r = ka.finalize()
+        ka.query(qkeys, out=q_out)
+        return r
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize(dev)
+    ka.timings(reset=True)
+    ka.set_profiling(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        info = step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ms_total, ws, dev)
+    timing = ka.timings(reset=True)
+    ka.set_profiling(False)
+    ms_step = ms_total / args.steps
+
+    # whole-job units: every valid window of the read set counted once across the ranks
+    W_total = rs.windows_upper_bound(k) if ws > 1 else int(info.valid_windows)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([int(info.valid_windows)], dtype=torch.int64, device=dev)
+        dist.all_reduce(t)
+        W_total = int(t.item())
+    value = W_total / (ms_step * 1e-3) / 1e9
+    positions = rs.n_bases + rs.n_reads
+    roof = roofline(timing, info, positions, load_peak(), args.steps)
+    kernel_ms = {k2[3:]: round(v / args.steps, 3) for k2, v in timing.items() if k2.startswith("ms_")}
+    launches = int(timing["launches"])
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, ka, rs, dev, qkeys, ws)
+    ka.destroy()
+    del seq, qual, offs
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+           "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+           "dtype": "u64", "data": "synthetic",
+           "config": {"workload": args.workload, "genome_bp": rs.meta["G"], "reads": rs.n_reads,
+                      "bases": rs.n_bases, "read_len": rs.meta["L"], "coverage": rs.meta["coverage"],
+                      "k": k, "min_depth": rs.meta["params"]["min_depth"], "bloom_fpr": 0.01,
+                      "valid_windows": int(info.valid_windows), "kmers_out": int(info.n),
+                      "uu_kmers": int(info.n_uu), "table_keys": int(info.table_keys),
+                      "queries_per_step": int(qkeys.shape[0]),
+                      "parallelism": f"owner-computes x{ws}" if ws > 1 else "1 GPU",
+                      "l2": "inputs (12 GB of reads, 33 GB table) far larger than L2; no flush"},
+           "roofline": roof, "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
+           "clocks": clk, "generation_s": round(t_gen, 1)}
+    if e2e:
+        out["e2e"] = e2e
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(rs, budget_s=args.cpu_budget)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def run_e2e(args, ka, rs, dev, qkeys_dev, ws):
+    """Same metric through the public API from pinned host buffers: host->device copies of the
+    reads, the whole path, and device->host copies of the records and query answers."""
+    import torch
+    seq_h = torch.from_numpy(rs.seq).pin_memory()
+    qual_h = torch.from_numpy(rs.qual).pin_memory()
+    offs_h = torch.from_numpy(rs.offsets.view(np.int64)).pin_memory()
+    qk_h = qkeys_dev.cpu().pin_memory()
+    qn = qk_h.shape[0]
+    q_counts = torch.empty(qn, dtype=torch.int32).pin_memory()
+    q_ext = torch.empty((qn, 8), dtype=torch.int32).pin_memory()
+    q_codes = torch.empty((qn, 2), dtype=torch.uint8).pin_memory()
+    import ctypes
+    from paper_1705_11147_gb300 import capi
+    lib = capi.load()
+    out_cap = int(ka.result_info.table_keys) + 1
+    r_keys = torch.empty((out_cap, 2), dtype=torch.int64).pin_memory()
+    r_counts = torch.empty(out_cap, dtype=torch.int32).pin_memory()
+    r_ext = torch.empty((out_cap, 8), dtype=torch.int32).pin_memory()
+    r_codes = torch.empty((out_cap, 2), dtype=torch.uint8).pin_memory()
+    seq_np, qual_np = seq_h.numpy(), qual_h.numpy()
+    offs_np = offs_h.numpy().view(np.uint64)
+
+    def step():
+        ka.reset()
+        capi.check(lib.kmer_analysis_count(ka.handle, seq_np.ctypes.data, qual_np.ctypes.data,
+                                           offs_np.ctypes.data, rs.n_reads, 0), "count")
+        r = ka.finalize()
+        capi.check(lib.kmer_analysis_copy_result(ka.handle, r_keys.data_ptr(), r_counts.data_ptr(),
+                                                 r_ext.data_ptr(), r_codes.data_ptr(), out_cap, 0),
+                   "copy_result")
+        capi.check(lib.kmer_analysis_query(ka.handle, qk_h.data_ptr(), qn, q_counts.data_ptr(),
+                                           q_ext.data_ptr(), q_codes.data_ptr(), 0), "query")
+        return r
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    t0 = time.perf_counter()
+    steps = max(1, min(args.steps, 3))
+    for _ in range(steps):
+        info = step()
+    torch.cuda.synchronize(dev)
+    dt = (time.perf_counter() - t0) / steps
+    dt = max_over_ranks(dt, ws, dev)
+    n = int(info.n)
+    h2d = rs.n_bases * 2 + (rs.n_reads + 1) * 8 + qn * 16
+    d2h = n * (16 + 4 + 32 + 2) + qn * (4 + 32 + 2)
+    return {"value": round(int(info.valid_windows) * (ws if ws > 1 else 1) / dt / 1e9, 3), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps,
+            "ms_per_step": round(dt * 1e3, 2)}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, ws, rank):
+    """The CPU oracle on the same workload, metric and unit; each step a bounded prefix of
+    the reads (rank 0 only)."""
+    if rank != 0:
+        return None
+    import oracle
+    rs = synth.workload(args.workload, scale=args.scale)
+    threads = os.cpu_count() or 1
+    p = dict(rs.meta["params"])
+    p.pop("bloom_fpr", None)
+    # calibrate a prefix so that warmup + steps fit a few minutes
+    cal = cpu_baseline(rs, budget_s=max(5.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1))),
+                       threads=threads)
+    n = int(cal["reads"])
+    offs = rs.offsets[: n + 1]
+    s, q = rs.seq[: int(offs[-1])], rs.qual[: int(offs[-1])]
+    for _ in range(args.warmup):
+        oracle.run(s, q, offs, threads=threads, **p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle.run(s, q, offs, threads=threads, **p)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = r.valid_windows / dt / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3, 1), "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "k": p["k"], "sample_reads": n,
+                       "sample_windows": int(r.valid_windows)},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": threads,
+                             "kind": "oracle", "sample": f"first {n} of {rs.n_reads} reads per step"},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large_200m", choices=list(synth.WORKLOADS))
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--queries", type=int, default=1_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        from paper_1705_11147_gb300 import build
+        build.build()
+        out = run_ours(args, ws, rank, local)
+    if out is not None and rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

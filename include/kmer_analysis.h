@@ -1,0 +1,228 @@
+/*
+ * kmer_analysis.h — C ABI of the GB300 k-mer analysis library (libkmer_analysis.so).
+ *
+ * The library implements the k-mer analysis stage of HipMer / Meraculous (arXiv 1705.11147):
+ *   - chopping reads into overlapping k-mers (Section 2, item 1; Figure "combined"(b)),
+ *   - canonical form (lexicographic min of a k-mer and its reverse complement),
+ *   - a Bloom-filter pass that keeps singleton (error) k-mers out of the hash table
+ *     (Section 5.1),
+ *   - exact counting in a device hash table with per-k-mer counts of high-quality left and
+ *     right extension bases (Section 5.1: two arrays of four counters per k-mer),
+ *   - the depth filter and classification of each side into A/C/G/T (unique), X (none,
+ *     Section 4.1) or F (fork, Section 2), the unique-extension (UU) set being the k-mers
+ *     with A/C/G/T on both sides (Section 5.2),
+ *   - a read-only lookup phase (Section 4.2, use case GRO).
+ *
+ * Conventions common to every entry point
+ *   - Return value: KMA_OK (0) or a negative KMA_E* code; kmer_analysis_strerror() names it.
+ *   - Work is enqueued on the CUDA stream given at create (cudaStream_t passed as void*;
+ *     NULL = legacy default stream). Calls return before the GPU finishes unless stated.
+ *   - `on_device` = 1: every pointer argument of that call is a device pointer (or managed
+ *     memory); 0: host pointers (pinned memory gives the fastest copies). The library never
+ *     keeps a caller pointer past the call: input bytes are packed into library-owned device
+ *     memory, so the caller may reuse its buffers once the call's stream work is done (host
+ *     inputs: once the call returns).
+ *   - A handle is not thread-safe; different handles may be used from different threads.
+ *   - k-mer keys are 2-bit codes A=0 C=1 G=2 T=3, first base most significant, as a 128-bit
+ *     number stored as two uint64 words {lo, hi}. k <= 32 keys have hi = 0.
+ *   - Side codes: 0..3 = A C G T (unique high-quality extension), 4 = X, 5 = F.
+ */
+#ifndef KMER_ANALYSIS_H
+#define KMER_ANALYSIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KMA_OK 0
+#define KMA_EINVAL (-1)    /* bad argument: k, thresholds, sizes, pointers, inconsistent offsets */
+#define KMA_ENOMEM (-2)    /* device allocation failed */
+#define KMA_EFULL (-3)     /* hash table or packed-read arena capacity exceeded: no partial result;
+                              recreate with a larger table_capacity / max_bases and count again */
+#define KMA_ESTATE (-4)    /* call not allowed in the handle's state (count after finalize, ...) */
+#define KMA_ETIMEOUT (-5)  /* reserved: the kernels contain no device-side waits */
+#define KMA_EOVERFLOW (-6) /* a 32-bit k-mer counter would have wrapped */
+#define KMA_ECUDA (-7)     /* a CUDA runtime call failed (cudaGetLastError text via strerror) */
+
+#define KMA_CODE_X 4
+#define KMA_CODE_F 5
+
+typedef struct kma_handle kma_handle;
+
+/* Counting parameters (Section 5.1: reads, k, error cutoff epsilon, threshold t_hq). */
+typedef struct {
+  uint32_t k;                 /* k-mer length, 1..63; odd when canonical = 1 (an even k admits
+                                 k-mers equal to their own reverse complement) */
+  uint32_t min_depth;         /* keep k-mers with count >= min_depth (paper: > epsilon) */
+  uint32_t min_ext_count;     /* an extension base is high quality if seen >= this many times
+                                 (paper: more than t_hq) */
+  uint8_t qual_threshold;     /* an extension base is counted only if its Phred >= this */
+  uint8_t qual_offset;        /* quality encoding offset: 33 for ASCII Phred+33, 0 for raw */
+  uint8_t use_bloom;          /* 1: Bloom-filter singleton pass (requires min_depth >= 2);
+                                 0: every k-mer goes straight into the table */
+  uint8_t canonical;          /* 1: canonical k-mers (default); 0: forward strand only */
+  uint64_t max_bases;         /* arena capacity: total bases over all count() calls */
+  uint64_t max_reads;         /* total reads over all count() calls (0: max_bases / 32) */
+  uint64_t expected_distinct; /* Bloom sizing: expected distinct k-mers incl. errors
+                                 (0: the number of windows max_bases allows) */
+  double bloom_fpr;           /* target false-positive rate of the Bloom filter (0: 0.01) */
+  uint64_t table_capacity;    /* hash-table slots (0: expected_keys / load_factor) */
+  uint64_t expected_keys;     /* keys the table must hold (0: expected_distinct, or the window
+                                 bound). With the Bloom pass only k-mers seen twice (plus
+                                 false positives) are inserted. */
+  double load_factor;         /* target table load when table_capacity = 0 (0: 0.5) */
+  uint64_t staging_bytes;     /* device staging buffer for host inputs (0: 256 MiB) */
+  /* Launch shape (0 = library default; chosen by the autotuner per GPU and size class). */
+  uint32_t block_threads;     /* threads per CTA of the counting kernels: 128..1024, x32 */
+  uint32_t windows_per_thread;/* window starts one thread handles per tile: 1..16 */
+  uint32_t ctas_per_sm;       /* persistent grid = SMs x ctas_per_sm (0: occupancy bound) */
+  uint32_t warp_aggregate;    /* 1: merge identical keys inside a warp before the atomics */
+  /* Owner-computes partition (Section 5.1: a deterministic k-mer -> owner map makes every
+   * owner's Bloom filter and table exact on its own). With n_parts > 1 the handle counts
+   * only k-mers whose owner is `part`; the union of the n_parts results is the whole result.
+   * The owner of a k-mer is a hash of its canonical key (library-defined, fixed). */
+  uint32_t n_parts;           /* 0 or 1: no partition */
+  uint32_t part;              /* 0 .. n_parts-1 */
+} kma_params;
+
+/* Sizes derived from a kma_params (pure host arithmetic, no GPU needed). */
+typedef struct {
+  uint64_t bloom_words;    /* 64-bit words of the blocked Bloom filter (0 without Bloom) */
+  uint32_t bloom_hashes;   /* bits set per k-mer, all inside one 64-bit word */
+  uint32_t reserved;
+  double bloom_fpr_est;    /* predicted false-positive rate at expected_distinct k-mers */
+  uint64_t table_slots;    /* hash-table slots, 64 bytes each */
+  uint64_t arena_positions;/* packed positions: bases + one separator per read + padding */
+  uint64_t device_bytes;   /* device memory a handle holds (all buffers) */
+} kma_plan;
+
+/* Result of finalize. Pointers are device memory owned by the handle, valid until the
+ * next finalize, reset or destroy. Record order is unspecified. */
+typedef struct {
+  uint64_t n;              /* k-mers with count >= min_depth */
+  uint64_t n_uu;           /* of those, unique high-quality extension on both sides */
+  uint64_t valid_windows;  /* windows (k-mer occurrences) counted */
+  uint64_t table_keys;     /* distinct keys in the table before the depth filter */
+  const uint64_t* keys;    /* [n][2] {lo, hi} */
+  const uint32_t* counts;  /* [n] */
+  const uint32_t* ext;     /* [n][8]: left A C G T, right A C G T */
+  const uint8_t* codes;    /* [n][2]: left code, right code */
+} kma_result;
+
+/* Sizes of a handle for `params` (Section 5.1 Bloom sizing: false-positive rate of a filter
+ * whose bits for one key share a 64-bit word). Host only. KMA_EINVAL on bad params. */
+int kmer_analysis_plan(const kma_params* params, kma_plan* out);
+
+/* Allocate a handle: packed-read arena, Bloom filter, hash table, status words, staging.
+ * `cuda_stream` is a cudaStream_t (NULL = default stream). The handle starts empty.
+ * Errors: KMA_EINVAL (params), KMA_ENOMEM, KMA_ECUDA. On error *out is NULL. */
+int kmer_analysis_create(const kma_params* params, void* cuda_stream, kma_handle** out);
+
+/* Add reads (Section 5.1 counting phase; may be called repeatedly with further batches).
+ * Read r is seq[offsets[r] .. offsets[r+1]) with qualities at the same positions of `qual`;
+ * offsets has n_reads + 1 non-decreasing entries. Bases other than A/C/G/T (either case)
+ * make every window covering them invalid. Reads shorter than k add no windows.
+ * Packs the reads 2 bits per base into the handle's arena and runs the first pass
+ * (Bloom test-and-set, table insert of k-mers seen twice; without Bloom, the counting).
+ * With on_device = 1 the call reads offsets[0] and offsets[n_reads] back, which waits for
+ * the stream up to that point. Errors: KMA_EINVAL (decreasing offsets), KMA_EFULL (arena:
+ * max_bases / max_reads exceeded; table overflow is reported by finalize), KMA_ESTATE
+ * (after finalize), KMA_ECUDA. */
+int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual,
+                        const uint64_t* offsets, uint64_t n_reads, int on_device);
+
+/* Finish counting: second pass over the retained reads (first sightings of k-mers the
+ * Bloom pass left out of the table), depth filter, classification and compaction into
+ * device arrays (see kma_result). Synchronises the stream. Errors: KMA_EFULL (table
+ * overflow: no partial result), KMA_EOVERFLOW, KMA_EINVAL (inconsistent offsets seen on
+ * the device), KMA_ESTATE (already finalized), KMA_ENOMEM, KMA_ECUDA. */
+int kmer_analysis_finalize(kma_handle* h, kma_result* out);
+
+/* Copy the finalized records into caller buffers of `capacity` records (host or device
+ * pointers, per on_device; any pointer may be NULL to skip that array). Synchronises.
+ * Errors: KMA_ESTATE (not finalized), KMA_EINVAL (capacity < n). */
+int kmer_analysis_copy_result(kma_handle* h, uint64_t* keys, uint32_t* counts, uint32_t* ext,
+                              uint8_t* codes, uint64_t capacity, int on_device);
+
+/* Look up n k-mers given as keys[n][2] in either orientation (read-only phase, Section
+ * 4.2 GRO). Answers are in the query's orientation: counts[i], ext[i][8] (left A C G T,
+ * right A C G T) and codes[i][2]; k-mers below min_depth or absent give count 0, zero
+ * extensions and codes X/X. Keys with bits set at or above bit 2k answer as absent.
+ * Errors: KMA_ESTATE (not finalized), KMA_EINVAL, KMA_ECUDA. */
+int kmer_analysis_query(kma_handle* h, const uint64_t* keys, uint64_t n, uint32_t* counts,
+                        uint32_t* ext, uint8_t* codes, int on_device);
+
+/* Empty the handle for a new read set with the same parameters, keeping its memory
+ * (arena, Bloom filter and table are cleared on the stream). */
+int kmer_analysis_reset(kma_handle* h);
+
+/* Change the stream later calls enqueue on (the caller orders the two streams). */
+int kmer_analysis_set_stream(kma_handle* h, void* cuda_stream);
+
+/* Status flags the device raised so far (table full, overflow, bad offsets) as a KMA_E*
+ * code, KMA_OK if none. Synchronises the stream. */
+int kmer_analysis_status(kma_handle* h);
+
+/* Device bytes the handle holds (arena, Bloom, table, staging, result buffers). */
+uint64_t kmer_analysis_device_bytes(const kma_handle* h);
+
+/* Per-kernel timing (tracing). With profiling enabled the library records a CUDA event pair
+ * around each of its kernel launches on the launching stream. kmer_analysis_timings
+ * synchronises, sums the elapsed times since the last reset and optionally resets them.
+ * Launch counts are kept whether or not profiling is enabled. */
+typedef struct {
+  double ms[8];           /* per kernel kind: see KMA_KERNEL_* */
+  uint64_t launches[8];   /* launches per kernel kind */
+  uint64_t total_launches;
+  uint64_t first_sightings; /* Bloom pass: windows that were the first sighting of their k-mer */
+} kma_timings;
+
+#define KMA_KERNEL_PACK 0
+#define KMA_KERNEL_PASS 1      /* first pass: Bloom test-and-set + table (or counting) */
+#define KMA_KERNEL_RECOUNT 2   /* second pass over first sightings */
+#define KMA_KERNEL_CLASSIFY 3
+#define KMA_KERNEL_QUERY 4
+#define KMA_KERNEL_INIT 5      /* table initialisation on create / reset */
+
+int kmer_analysis_set_profiling(kma_handle* h, int enable);
+int kmer_analysis_timings(kma_handle* h, kma_timings* out, int reset);
+
+/* Free everything (waits for the handle's stream). NULL is a no-op. */
+void kmer_analysis_destroy(kma_handle* h);
+
+const char* kmer_analysis_strerror(int code);
+
+/* ---- Batched counting: many independent read sets in one persistent launch ----------
+ * Each handle keeps its own arena, Bloom filter and table (per-sample partitions); the
+ * counting kernels take all of them at once, so small samples share the GPU instead of
+ * each paying its own launches and synchronisations. All handles must have been created
+ * on the same device; work is enqueued on hs[0]'s stream (the caller orders the other
+ * handles' streams before it). Up to KMA_MAX_BATCH handles per call.
+ * kmer_analysis_count_batch takes device pointers only and does not synchronise, so it can
+ * be captured into a CUDA graph: n_bases must equal offsets[n_reads] - offsets[0]
+ * (checked on the device; a mismatch makes finalize return KMA_EINVAL). */
+#define KMA_MAX_BATCH 64
+
+typedef struct {
+  const char* seq;
+  const char* qual;
+  const uint64_t* offsets; /* n_reads + 1 entries */
+  uint64_t n_reads;
+  uint64_t n_bases;
+} kma_reads;
+
+int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uint32_t n);
+
+/* Finalize several handles with one launch per phase; out[i] receives handle i's result.
+ * Synchronises hs[0]'s stream. Errors as kmer_analysis_finalize; the first failing
+ * handle's code is returned and the others are still finalized. */
+int kmer_analysis_finalize_batch(kma_handle* const* hs, uint32_t n, kma_result* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMER_ANALYSIS_H */

@@ -35,6 +35,9 @@
 #include <array>
 #include <cstdint>
 #include <cstring>
+#include <memory>
+#include <memory_resource>
+#include <sys/mman.h>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -65,7 +68,33 @@ struct KeyHash {
   }
 };
 
-using Map = std::unordered_map<Key, Rec, KeyHash>;
+// Each thread's map draws its nodes from its own monotonic arena (large chunks), so counting
+// threads do not contend on the system allocator.
+using Map = std::pmr::unordered_map<Key, Rec, KeyHash>;
+
+// Upstream of the arenas: 2 MiB-aligned blocks marked for transparent huge pages, so that
+// touching fresh node memory costs few page faults.
+class HugeBlocks : public std::pmr::memory_resource {
+  void* do_allocate(size_t bytes, size_t) override {
+    const size_t a = size_t(2) << 20;
+    void* p = std::aligned_alloc(a, (bytes + a - 1) / a * a);
+    if (!p) throw std::bad_alloc();
+    madvise(p, (bytes + a - 1) / a * a, MADV_HUGEPAGE);
+    return p;
+  }
+  void do_deallocate(void* p, size_t, size_t) override { std::free(p); }
+  bool do_is_equal(const std::pmr::memory_resource& o) const noexcept override { return this == &o; }
+};
+
+HugeBlocks g_huge_blocks;
+
+struct ArenaMap {
+  std::unique_ptr<std::pmr::monotonic_buffer_resource> arena;
+  std::unique_ptr<Map> map;
+  ArenaMap()
+      : arena(new std::pmr::monotonic_buffer_resource(size_t(64) << 20, &g_huge_blocks)),
+        map(new Map(arena.get())) {}
+};
 
 char fold(uint8_t c) { return (c >= 'a' && c <= 'z') ? (char)(c - 'a' + 'A') : (char)c; }
 
@@ -120,27 +149,47 @@ bool usable(const std::string& s, const uint8_t* q, int64_t j, const Params& p) 
   return (int)q[j] - (int)p.qual_offset >= (int)p.qual_threshold;
 }
 
+Key pack_chars(const char* key, int64_t k) {
+  unsigned __int128 v = 0;
+  for (int64_t j = 0; j < k; ++j) v = (v << 2) | (unsigned __int128)code_of(key[j]);
+  return Key{(uint64_t)v, (uint64_t)(v >> 64)};
+}
+
+uint64_t fnv1a_chars(const char* s, int64_t n) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (int64_t j = 0; j < n; ++j) h = (h ^ (uint8_t)s[j]) * 0x100000001b3ull;
+  return h;
+}
+
 // Steps 1-4 over reads [r0, r1) into map m; returns the number of valid windows seen
-// (before partition filtering).
+// (before partition filtering). Windows and their reverse complements are built in
+// fixed-size character buffers (k <= 63), so no step allocates per window.
 uint64_t count_reads(const uint8_t* seq, const uint8_t* qual, const uint64_t* offsets,
                      uint64_t r0, uint64_t r1, const Params& p, uint32_t part,
                      uint32_t n_parts, Map& m) {
   uint64_t valid_windows = 0;
   const int64_t k = p.k;
+  std::string s;
+  std::vector<int64_t> bad;  // bad[j] = number of non-ACGT characters in s[0, j)
+  char rc[64];
   for (uint64_t r = r0; r < r1; ++r) {
     const int64_t L = (int64_t)(offsets[r + 1] - offsets[r]);
     const uint8_t* q = qual + offsets[r];
-    std::string s(L, ' ');
-    for (int64_t j = 0; j < L; ++j) s[(size_t)j] = fold(seq[offsets[r] + j]);
+    s.assign((size_t)L, ' ');
+    bad.assign((size_t)L + 1, 0);
+    for (int64_t j = 0; j < L; ++j) {
+      s[(size_t)j] = fold(seq[offsets[r] + j]);
+      bad[(size_t)j + 1] = bad[(size_t)j] + (is_acgt(s[(size_t)j]) ? 0 : 1);
+    }
     for (int64_t i = 0; i + k <= L; ++i) {
-      std::string w = s.substr((size_t)i, (size_t)k);
-      if (!std::all_of(w.begin(), w.end(), is_acgt)) continue;
+      if (bad[(size_t)(i + k)] != bad[(size_t)i]) continue;  // window has a non-ACGT character
       ++valid_windows;
-      std::string rc = reverse_complement(w);
-      const bool forward = !p.canonical || w <= rc;
-      const std::string& key = forward ? w : rc;
-      if (n_parts > 1 && fnv1a(key) % n_parts != part) continue;
-      Rec& rec = m[pack(key)];
+      const char* w = s.data() + i;
+      for (int64_t j = 0; j < k; ++j) rc[j] = complement(w[k - 1 - j]);
+      const bool forward = !p.canonical || std::memcmp(w, rc, (size_t)k) <= 0;
+      const char* key = forward ? w : rc;
+      if (n_parts > 1 && fnv1a_chars(key, k) % n_parts != part) continue;
+      Rec& rec = m[pack_chars(key, k)];
       rec.count += 1;
       const bool left_ok = usable(s, q, i - 1, p);
       const bool right_ok = usable(s, q, i + k, p);
@@ -172,8 +221,16 @@ struct Result {
   uint64_t valid_windows = 0;
   std::vector<Key> keys;
   std::vector<Rec> recs;
-  Map table;  // all counted keys (before the min_depth filter), kept for queries
+  // all counted keys (before the min_depth filter), split by KeyHash % parts.size()
+  std::vector<ArenaMap> parts;
+  const Rec* find(const Key& k) const {
+    const Map& m = *parts[KeyHash()(k) % parts.size()].map;
+    auto it = m.find(k);
+    return it == m.end() ? nullptr : &it->second;
+  }
 };
+
+bool key_less(const Key& a, const Key& b) { return a[1] != b[1] ? a[1] < b[1] : a[0] < b[0]; }
 
 }  // namespace
 
@@ -190,41 +247,57 @@ void* oracle_run(const uint8_t* seq, const uint8_t* qual, const uint64_t* offset
            op->canonical};
   if (n_parts == 0) n_parts = 1;
   if (n_threads < 1) n_threads = 1;
-  if ((uint64_t)n_threads > n_reads) n_threads = n_reads ? (int)n_reads : 1;
-  std::vector<Map> maps((size_t)n_threads);
-  std::vector<uint64_t> windows((size_t)n_threads, 0);
-  std::vector<std::thread> th;
-  for (int t = 0; t < n_threads; ++t) {
-    uint64_t r0 = n_reads * (uint64_t)t / (uint64_t)n_threads;
-    uint64_t r1 = n_reads * (uint64_t)(t + 1) / (uint64_t)n_threads;
-    th.emplace_back([&, t, r0, r1] {
-      windows[(size_t)t] = count_reads(seq, qual, offsets, r0, r1, p, part, n_parts, maps[(size_t)t]);
-    });
+  const size_t T = (size_t)n_threads;
+  // 1. each thread counts the windows of its share of the reads (steps 1-4)
+  std::vector<ArenaMap> maps(T);
+  std::vector<uint64_t> windows(T, 0);
+  {
+    std::vector<std::thread> th;
+    for (size_t t = 0; t < T; ++t) {
+      const uint64_t r0 = n_reads * t / T, r1 = n_reads * (t + 1) / T;
+      th.emplace_back([&, t, r0, r1] {
+        windows[t] = count_reads(seq, qual, offsets, r0, r1, p, part, n_parts, *maps[t].map);
+      });
+    }
+    for (auto& x : th) x.join();
   }
-  for (auto& x : th) x.join();
+  // 2. merge: thread u sums every key with KeyHash % T == u over all thread maps
   Result* res = new Result();
   res->p = p;
-  Map& all = res->table;
-  all = std::move(maps[0]);
-  res->valid_windows = windows[0];
-  for (size_t t = 1; t < maps.size(); ++t) {
-    res->valid_windows += windows[t];
-    for (auto& kv : maps[t]) {
-      Rec& r = all[kv.first];
-      r.count += kv.second.count;
-      for (int j = 0; j < 8; ++j) r.ext[j] += kv.second.ext[j];
+  for (size_t t = 0; t < T; ++t) res->valid_windows += windows[t];
+  res->parts.resize(T);
+  std::vector<std::vector<std::pair<Key, Rec>>> kept(T);
+  {
+    std::vector<std::thread> th;
+    for (size_t u = 0; u < T; ++u) {
+      th.emplace_back([&, u] {
+        Map& dst = *res->parts[u].map;
+        for (size_t t = 0; t < T; ++t)
+          for (const auto& kv : *maps[t].map) {
+            if (KeyHash()(kv.first) % T != u) continue;
+            Rec& r = dst[kv.first];
+            r.count += kv.second.count;
+            for (int j = 0; j < 8; ++j) r.ext[j] += kv.second.ext[j];
+          }
+        // 3. depth filter (step 5)
+        for (const auto& kv : dst)
+          if (kv.second.count >= p.min_depth) kept[u].push_back(kv);
+      });
     }
-    Map().swap(maps[t]);
+    for (auto& x : th) x.join();
   }
-  std::vector<std::pair<Key, Rec>> kept;
-  for (auto& kv : all)
-    if (kv.second.count >= p.min_depth) kept.push_back(kv);
-  std::sort(kept.begin(), kept.end(), [](const std::pair<Key, Rec>& a, const std::pair<Key, Rec>& b) {
-    return a.first[1] != b.first[1] ? a.first[1] < b.first[1] : a.first[0] < b.first[0];
+  std::vector<ArenaMap>().swap(maps);
+  std::vector<std::pair<Key, Rec>> all;
+  for (auto& v : kept) {
+    all.insert(all.end(), v.begin(), v.end());
+    std::vector<std::pair<Key, Rec>>().swap(v);
+  }
+  std::sort(all.begin(), all.end(), [](const std::pair<Key, Rec>& a, const std::pair<Key, Rec>& b) {
+    return key_less(a.first, b.first);
   });
-  res->keys.reserve(kept.size());
-  res->recs.reserve(kept.size());
-  for (auto& kv : kept) res->keys.push_back(kv.first), res->recs.push_back(kv.second);
+  res->keys.reserve(all.size());
+  res->recs.reserve(all.size());
+  for (auto& kv : all) res->keys.push_back(kv.first), res->recs.push_back(kv.second);
   return res;
 }
 
@@ -255,19 +328,19 @@ void oracle_query(void* h, const uint64_t* qkeys, uint64_t n, uint32_t* counts, 
     std::string w = unpack(Key{qkeys[2 * i], qkeys[2 * i + 1]}, p.k);
     std::string rc = reverse_complement(w);
     const bool forward = !p.canonical || w <= rc;
-    auto it = r->table.find(pack(forward ? w : rc));
+    const Rec* rec = r->find(pack(forward ? w : rc));
     uint32_t e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint32_t c = 0;
-    if (it != r->table.end() && it->second.count >= p.min_depth) {
-      c = it->second.count;
+    if (rec && rec->count >= p.min_depth) {
+      c = rec->count;
       for (int b = 0; b < 4; ++b) {
         if (forward) {
-          e[b] = it->second.ext[b];
-          e[4 + b] = it->second.ext[4 + b];
+          e[b] = rec->ext[b];
+          e[4 + b] = rec->ext[4 + b];
         } else {
           // the query's left neighbours are the complements of the key's right neighbours
-          e[code_of(complement("ACGT"[b]))] = it->second.ext[4 + b];
-          e[4 + code_of(complement("ACGT"[b]))] = it->second.ext[b];
+          e[code_of(complement("ACGT"[b]))] = rec->ext[4 + b];
+          e[4 + code_of(complement("ACGT"[b]))] = rec->ext[b];
         }
       }
     }

@@ -1,0 +1,836 @@
+// Host side of the C ABI declared in include/kmer_analysis.h: parameter checks, sizing
+// (Bloom filter, table, arena), device memory, staging of host inputs, launch sequencing
+// and status reporting. Every computation on reads and k-mers runs in kma_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/kmer_analysis.h"
+#include "kma_internal.cuh"
+
+using namespace kma;
+typedef unsigned long long u64;
+
+namespace {
+
+thread_local std::string g_last_cuda_error;
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_cuda_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return KMA_ECUDA;
+}
+
+#define KMA_CUDA(call)                                        \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+  } while (0)
+
+constexpr u64 kArenaSlack = 64ull * 4096;  // padding positions for per-batch 64-alignment
+constexpr u64 kDefaultStaging = 256ull << 20;
+
+// ------------------------------------------------------------------ Bloom sizing
+//
+// Section 5.1 sizes the filter from the number of distinct k-mers m, the filter size n and
+// h hash functions with Pr(e) = (1 - e^{-h m / n})^h, optimal h = ln 2 * n / m (the printed
+// version swaps m and n in the exponent and in h; this is the standard form). Here all h
+// bits of a k-mer lie in one 64-bit word (so one atomicOr is a linearisable test-and-set),
+// which raises the rate: a word receives j other k-mers with j ~ Poisson(m / W) for W words,
+// and given j the probability that one bit is set is 1 - (63/64)^{h j}. The estimate is the
+// Poisson mixture of (1 - (63/64)^{h j})^h.
+double blocked_fpr(double m, double words, unsigned h) {
+  if (words <= 0) return 1.0;
+  const double lam = m / words;
+  const double q = std::log(63.0 / 64.0);
+  // sum the Poisson(lam) pmf over lam +- 12 sd (+40); the mass outside counts as certain
+  // false positives, which only makes the estimate conservative
+  const double sd = std::sqrt(lam);
+  const long j0 = (long)std::max(0.0, std::floor(lam - 12.0 * sd - 40.0));
+  const long j1 = (long)std::ceil(lam + 12.0 * sd + 40.0);
+  double fpr = 0.0, mass = 0.0;
+  for (long j = j0; j <= j1; ++j) {
+    const double pmf = lam > 0 ? std::exp(-lam + (double)j * std::log(lam) - std::lgamma((double)j + 1.0))
+                               : (j == 0 ? 1.0 : 0.0);
+    mass += pmf;
+    fpr += pmf * std::pow(1.0 - std::exp(q * h * (double)j), (double)h);
+  }
+  return std::min(1.0, fpr + std::max(0.0, 1.0 - mass));
+}
+
+void size_bloom(double m, double target, uint64_t& words, uint32_t& hbits, double& est) {
+  words = 0;
+  hbits = 0;
+  est = 1.0;
+  if (m < 1) m = 1;
+  for (unsigned h = 1; h <= 10; ++h) {
+    // smallest W with blocked_fpr <= target (monotone in W)
+    double lo = 1, hi = std::max(1.0, m / 64.0);  // start at one bit per key
+    while (blocked_fpr(m, hi, h) > target && hi < 1e15) hi *= 2;
+    if (blocked_fpr(m, hi, h) > target) continue;
+    lo = std::max(1.0, hi / 2);
+    while (hi - lo > std::max(1.0, hi * 1e-4)) {
+      const double mid = std::floor((lo + hi) / 2);
+      if (blocked_fpr(m, mid, h) <= target) hi = mid; else lo = mid;
+    }
+    const uint64_t w = (uint64_t)std::ceil(hi);
+    if (words == 0 || w < words) {
+      words = w;
+      hbits = h;
+      est = blocked_fpr(m, (double)w, h);
+    }
+  }
+}
+
+struct Derived {
+  kma_plan plan;
+  u64 codes_words, bit_words, mark_words;
+  u64 staging;
+};
+
+int check_params(const kma_params* p) {
+  if (!p) return KMA_EINVAL;
+  if (p->k < 1 || p->k > 63) return KMA_EINVAL;
+  if (p->canonical && (p->k % 2 == 0)) return KMA_EINVAL;
+  if (p->min_depth < 1) return KMA_EINVAL;
+  if (p->use_bloom && p->min_depth < 2) return KMA_EINVAL;
+  if (p->bloom_fpr < 0 || p->bloom_fpr >= 1) return KMA_EINVAL;
+  if (p->load_factor < 0 || p->load_factor > 0.95) return KMA_EINVAL;
+  if (p->max_bases == 0) return KMA_EINVAL;
+  if (p->block_threads && (p->block_threads < 128 || p->block_threads > 1024 || p->block_threads % 32))
+    return KMA_EINVAL;
+  if (p->windows_per_thread > 16) return KMA_EINVAL;
+  if (p->n_parts > 1 && p->part >= p->n_parts) return KMA_EINVAL;
+  return KMA_OK;
+}
+
+int derive(const kma_params* p, Derived& d) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  std::memset(&d, 0, sizeof(d));
+  const u64 windows_bound = p->max_bases;
+  const double distinct = p->expected_distinct ? (double)p->expected_distinct : (double)windows_bound;
+  if (p->use_bloom) {
+    const double target = p->bloom_fpr > 0 ? p->bloom_fpr : 0.01;
+    size_bloom(distinct, target, d.plan.bloom_words, d.plan.bloom_hashes, d.plan.bloom_fpr_est);
+    if (d.plan.bloom_words == 0) return KMA_EINVAL;
+  }
+  if (p->table_capacity) {
+    d.plan.table_slots = p->table_capacity;
+  } else {
+    const double keys = p->expected_keys ? (double)p->expected_keys : distinct;
+    const double lf = p->load_factor > 0 ? p->load_factor : 0.5;
+    d.plan.table_slots = (u64)std::ceil(keys / lf) + 64;
+  }
+  const u64 reads = p->max_reads ? p->max_reads : p->max_bases / 32 + 1;
+  const u64 pos = ((p->max_bases + reads + kArenaSlack + 63) / 64) * 64;
+  d.plan.arena_positions = pos;
+  d.codes_words = pos / 32 + 4;
+  d.bit_words = pos / 64 + 4;
+  d.mark_words = pos / 32 + 4;
+  d.staging = p->staging_bytes ? p->staging_bytes : kDefaultStaging;
+  d.plan.device_bytes = d.codes_words * 8 + 2 * d.bit_words * 8 + d.mark_words * 4 +
+                        d.plan.bloom_words * 8 + d.plan.table_slots * sizeof(Slot) +
+                        sizeof(DevStatus) + 2 * (2 * d.staging + (d.staging / 16 + 2) * 8);
+  return KMA_OK;
+}
+
+// Library-private stream-ordered pool per device: handles of a serving loop come and go,
+// and freed blocks are reused instead of going back to the driver.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64];
+bool g_pool_init[64];
+
+int get_pool(int dev, cudaMemPool_t* out) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (dev < 0 || dev >= 64) return KMA_EINVAL;
+  if (!g_pool_init[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    KMA_CUDA(cudaMemPoolCreate(&g_pools[dev], &props));
+    u64 thr = ~0ull;
+    KMA_CUDA(cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &thr));
+    g_pool_init[dev] = true;
+  }
+  *out = g_pools[dev];
+  return KMA_OK;
+}
+
+}  // namespace
+
+struct kma_handle {
+  kma_params p;
+  Derived d;
+  cudaStream_t stream = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  cudaEvent_t consumed[2] = {nullptr, nullptr};
+  int device = 0;
+  int num_sms = 0;
+  cudaMemPool_t pool = nullptr;
+  LaunchShape shape{256, 4, 0};
+  bool agg = false;
+
+  u64* codes = nullptr;
+  u64* inv = nullptr;
+  u64* hq = nullptr;
+  unsigned* marks = nullptr;
+  u64* bloom = nullptr;
+  Slot* table = nullptr;
+  DevStatus* status = nullptr;
+  DevStatus* host_status = nullptr;  // pinned
+  unsigned char* stage_seq[2] = {nullptr, nullptr};
+  unsigned char* stage_qual[2] = {nullptr, nullptr};
+  u64* stage_offs[2] = {nullptr, nullptr};
+  u64 stage_offs_cap = 0;
+  int stage_next = 0;
+
+  u64 q_used = 0, reads_used = 0, bases_used = 0;
+  bool finalized = false;
+  bool failed = false;
+
+  u64* out_keys = nullptr;
+  unsigned* out_counts = nullptr;
+  unsigned* out_ext = nullptr;
+  unsigned char* out_codes = nullptr;
+  u64 out_cap = 0;
+  kma_result res;
+
+  // tracing
+  bool profiling = false;
+  struct ProfRec { int kind; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> event_pool;
+  double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  u64 launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+template <typename T>
+int dalloc(kma_handle* h, T** ptr, u64 count) {
+  *ptr = nullptr;
+  if (count == 0) return KMA_OK;
+  cudaError_t e = cudaMallocFromPoolAsync((void**)ptr, count * sizeof(T), h->pool, h->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return e == cudaErrorMemoryAllocation ? KMA_ENOMEM : cuda_fail(e, "cudaMallocFromPoolAsync");
+  }
+  return KMA_OK;
+}
+
+template <typename T>
+void dfree(kma_handle* h, T*& ptr) {
+  if (ptr) cudaFreeAsync(ptr, h->stream);
+  ptr = nullptr;
+}
+
+cudaEvent_t take_event(kma_handle* h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch one library kernel on `stream`, counting it and (when profiling) bracketing it
+// with a pair of CUDA events on that stream.
+template <typename F>
+int timed_launch(kma_handle* h, int kind, cudaStream_t stream, bool has_work, F&& launch) {
+  if (!has_work) return KMA_OK;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (h->profiling) {
+    a = take_event(h);
+    b = take_event(h);
+    if (a) cudaEventRecord(a, stream);
+  }
+  cudaError_t e = launch();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  h->launches[kind]++;
+  if (h->profiling && a && b) {
+    cudaEventRecord(b, stream);
+    h->prof.push_back({kind, a, b});
+  }
+  return KMA_OK;
+}
+
+void free_all(kma_handle* h) {
+  dfree(h, h->codes); dfree(h, h->inv); dfree(h, h->hq); dfree(h, h->marks);
+  dfree(h, h->bloom); dfree(h, h->table); dfree(h, h->status);
+  for (int i = 0; i < 2; ++i) { dfree(h, h->stage_seq[i]); dfree(h, h->stage_qual[i]); dfree(h, h->stage_offs[i]); }
+  dfree(h, h->out_keys); dfree(h, h->out_counts); dfree(h, h->out_ext); dfree(h, h->out_codes);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->host_status) cudaFreeHost(h->host_status);
+  h->host_status = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    if (h->copied[i]) cudaEventDestroy(h->copied[i]);
+    if (h->consumed[i]) cudaEventDestroy(h->consumed[i]);
+    h->copied[i] = h->consumed[i] = nullptr;
+  }
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  h->copy_stream = nullptr;
+  for (auto& r : h->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  h->prof.clear();
+  for (auto e : h->event_pool) cudaEventDestroy(e);
+  h->event_pool.clear();
+}
+
+int clear_state(kma_handle* h) {
+  KMA_CUDA(cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->stream));
+  if (h->bloom) KMA_CUDA(cudaMemsetAsync(h->bloom, 0, h->d.plan.bloom_words * 8, h->stream));
+  int rc = timed_launch(h, KMA_KERNEL_INIT, h->stream, h->d.plan.table_slots > 0,
+                        [&] { return launch_table_init(h->table, h->d.plan.table_slots, h->stream); });
+  if (rc) return rc;
+  // The arena is rewritten by each count(); only the slack words past the used range are
+  // read by windows near the end, and those must read as invalid.
+  KMA_CUDA(cudaMemsetAsync(h->inv, 0xFF, h->d.bit_words * 8, h->stream));
+  KMA_CUDA(cudaMemsetAsync(h->codes, 0, h->d.codes_words * 8, h->stream));
+  KMA_CUDA(cudaMemsetAsync(h->hq, 0, h->d.bit_words * 8, h->stream));
+  h->q_used = h->reads_used = h->bases_used = 0;
+  h->finalized = false;
+  h->failed = false;
+  std::memset(&h->res, 0, sizeof(h->res));
+  return KMA_OK;
+}
+
+void choose_shape(kma_handle* h) {
+  h->shape.block_threads = h->p.block_threads ? (int)h->p.block_threads : 256;
+  h->shape.windows_per_thread = h->p.windows_per_thread ? (int)h->p.windows_per_thread : 4;
+  h->agg = h->p.warp_aggregate != 0;
+  int per_sm = h->p.ctas_per_sm ? (int)h->p.ctas_per_sm
+                                : pass_max_ctas_per_sm(h->shape.block_threads, h->shape.windows_per_thread, h->agg);
+  if (per_sm < 1) per_sm = 1;
+  h->shape.grid = h->num_sms * per_sm;
+}
+
+int flags_to_code(unsigned flags) {
+  if (flags & kFlagBadOffsets) return KMA_EINVAL;
+  if (flags & kFlagFull) return KMA_EFULL;
+  if (flags & kFlagOverflow) return KMA_EOVERFLOW;
+  return KMA_OK;
+}
+
+int read_status(kma_handle* h) {
+  KMA_CUDA(cudaMemcpyAsync(h->host_status, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+  KMA_CUDA(cudaStreamSynchronize(h->stream));
+  return KMA_OK;
+}
+
+PassDesc pass_desc(kma_handle* h, unsigned mode, u64 q0, u64 q1) {
+  PassDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.codes = h->codes; d.inv = h->inv; d.hq = h->hq; d.marks = h->marks;
+  d.bloom = h->bloom; d.table = h->table; d.status = h->status;
+  d.bloom_words = h->d.plan.bloom_words; d.slots = h->d.plan.table_slots;
+  d.q0 = q0; d.q1 = q1;
+  d.k = h->p.k; d.bloom_h = h->d.plan.bloom_hashes; d.canonical = h->p.canonical;
+  d.mode = mode;
+  d.n_parts = h->p.n_parts > 1 ? h->p.n_parts : 1;
+  d.part = h->p.n_parts > 1 ? h->p.part : 0;
+  return d;
+}
+
+// Reserve arena space for a batch and describe it for the pack kernel.
+int reserve_batch(kma_handle* h, u64 n_reads, u64 n_bases, PackDesc& pd, u64& q0, u64& n_pos) {
+  n_pos = ((n_bases + n_reads + 63) / 64) * 64;
+  if (n_pos == 0) n_pos = 64;
+  if (h->q_used + n_pos + 256 > h->d.plan.arena_positions) return KMA_EFULL;
+  if (h->bases_used + n_bases > h->p.max_bases) return KMA_EFULL;
+  q0 = h->q_used;
+  std::memset(&pd, 0, sizeof(pd));
+  pd.n_reads = n_reads; pd.n_bases = n_bases; pd.q0 = q0; pd.n_pos = n_pos;
+  pd.codes = h->codes; pd.inv = h->inv; pd.hq = h->hq; pd.status = h->status;
+  pd.qual_min = (unsigned)h->p.qual_offset + (unsigned)h->p.qual_threshold;
+  h->q_used += n_pos;
+  h->reads_used += n_reads;
+  h->bases_used += n_bases;
+  return KMA_OK;
+}
+
+int run_pack_and_pass(kma_handle* h, const PackDesc& pd) {
+  PackBatch pb;
+  std::memset(&pb, 0, offsetof(PackBatch, d) + sizeof(PackDesc));
+  pb.n = 1;
+  pb.d[0] = pd;
+  pb.d[0].word_begin = 0;
+  pb.total_words = pd.n_pos / 64;
+  int rc = timed_launch(h, KMA_KERNEL_PACK, h->stream, pb.total_words > 0,
+                        [&] { return launch_pack(pb, h->stream, h->num_sms); });
+  if (rc) return rc;
+  PassBatch b;
+  std::memset(&b, 0, offsetof(PassBatch, d) + sizeof(PassDesc));
+  b.n = 1;
+  b.d[0] = pass_desc(h, h->p.use_bloom ? kModeBloom : kModeCount, pd.q0, pd.q0 + pd.n_pos);
+  const u64 tile = (u64)h->shape.block_threads * h->shape.windows_per_thread;
+  b.d[0].tile_begin = 0;
+  b.total_tiles = (pd.n_pos + tile - 1) / tile;
+  return timed_launch(h, KMA_KERNEL_PASS, h->stream, b.total_tiles > 0,
+                      [&] { return launch_pass(b, h->shape, h->agg, h->stream); });
+}
+
+int ensure_output(kma_handle* h, u64 need) {
+  if (need <= h->out_cap && h->out_keys) return KMA_OK;
+  dfree(h, h->out_keys); dfree(h, h->out_counts); dfree(h, h->out_ext); dfree(h, h->out_codes);
+  h->out_cap = 0;
+  u64 cap = std::max<u64>(need + need / 8, 1024);
+  int rc;
+  if ((rc = dalloc(h, &h->out_keys, 2 * cap))) return rc;
+  if ((rc = dalloc(h, &h->out_counts, cap))) return rc;
+  if ((rc = dalloc(h, &h->out_ext, 8 * cap))) return rc;
+  if ((rc = dalloc(h, &h->out_codes, 2 * cap))) return rc;
+  h->out_cap = cap;
+  return KMA_OK;
+}
+
+ClassDesc class_desc(kma_handle* h) {
+  ClassDesc c;
+  std::memset(&c, 0, sizeof(c));
+  c.table = h->table; c.status = h->status; c.slots = h->d.plan.table_slots;
+  c.out_keys = h->out_keys; c.out_counts = h->out_counts; c.out_ext = h->out_ext;
+  c.out_codes = h->out_codes; c.out_cap = h->out_cap;
+  c.min_depth = h->p.min_depth;
+  c.min_ext = h->p.min_ext_count ? h->p.min_ext_count : 1;
+  return c;
+}
+
+constexpr u64 kClassTile = 256 * 4;  // slots per classify block tile (kernel constants)
+
+void fill_result(kma_handle* h) {
+  kma_result& r = h->res;
+  r.n = h->host_status->n_out;
+  r.n_uu = h->host_status->n_uu;
+  r.valid_windows = h->host_status->valid_windows;
+  r.table_keys = h->host_status->table_keys;
+  r.keys = (const uint64_t*)h->out_keys;
+  r.counts = h->out_counts;
+  r.ext = h->out_ext;
+  r.codes = h->out_codes;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kmer_analysis_plan(const kma_params* params, kma_plan* out) {
+  if (!out) return KMA_EINVAL;
+  Derived d;
+  int rc = derive(params, d);
+  if (rc) return rc;
+  *out = d.plan;
+  return KMA_OK;
+}
+
+int kmer_analysis_create(const kma_params* params, void* cuda_stream, kma_handle** out) {
+  if (!out) return KMA_EINVAL;
+  *out = nullptr;
+  Derived d;
+  int rc = derive(params, d);
+  if (rc) return rc;
+  kma_handle* h = new kma_handle();
+  h->p = *params;
+  h->d = d;
+  h->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
+  if ((rc = get_pool(h->device, &h->pool))) { delete h; return rc; }
+  choose_shape(h);
+  h->stage_offs_cap = d.staging / 16 + 2;
+  if ((rc = dalloc(h, &h->codes, d.codes_words)) || (rc = dalloc(h, &h->inv, d.bit_words)) ||
+      (rc = dalloc(h, &h->hq, d.bit_words)) || (rc = dalloc(h, &h->marks, d.mark_words)) ||
+      (rc = dalloc(h, &h->bloom, d.plan.bloom_words)) ||
+      (rc = dalloc(h, &h->table, d.plan.table_slots)) || (rc = dalloc(h, &h->status, 1))) {
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  e = cudaMallocHost((void**)&h->host_status, sizeof(DevStatus));
+  if (e != cudaSuccess) { free_all(h); delete h; return cuda_fail(e, "cudaMallocHost"); }
+  std::memset(h->host_status, 0, sizeof(DevStatus));
+  if ((rc = clear_state(h))) { free_all(h); delete h; return rc; }
+  *out = h;
+  return KMA_OK;
+}
+
+static int setup_staging(kma_handle* h) {
+  if (h->stage_seq[0]) return KMA_OK;
+  int rc;
+  for (int i = 0; i < 2; ++i) {
+    if ((rc = dalloc(h, &h->stage_seq[i], h->d.staging)) || (rc = dalloc(h, &h->stage_qual[i], h->d.staging)) ||
+        (rc = dalloc(h, &h->stage_offs[i], h->stage_offs_cap)))
+      return rc;
+    KMA_CUDA(cudaEventCreateWithFlags(&h->copied[i], cudaEventDisableTiming));
+    KMA_CUDA(cudaEventCreateWithFlags(&h->consumed[i], cudaEventDisableTiming));
+  }
+  KMA_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+  // the staging buffers were allocated on h->stream: make the copy stream wait for that
+  KMA_CUDA(cudaEventRecord(h->consumed[0], h->stream));
+  KMA_CUDA(cudaEventRecord(h->consumed[1], h->stream));
+  return KMA_OK;
+}
+
+int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual, const uint64_t* offsets,
+                        uint64_t n_reads, int on_device) {
+  if (!h) return KMA_EINVAL;
+  if (h->finalized || h->failed) return KMA_ESTATE;
+  if (!offsets) return KMA_EINVAL;
+  if (n_reads == 0) return KMA_OK;
+  if (!seq || !qual) return KMA_EINVAL;
+  int rc;
+  if (on_device) {
+    u64 ends[2];
+    KMA_CUDA(cudaMemcpyAsync(&ends[0], offsets, 8, cudaMemcpyDeviceToHost, h->stream));
+    KMA_CUDA(cudaMemcpyAsync(&ends[1], offsets + n_reads, 8, cudaMemcpyDeviceToHost, h->stream));
+    KMA_CUDA(cudaStreamSynchronize(h->stream));
+    if (ends[1] < ends[0]) return KMA_EINVAL;
+    PackDesc pd;
+    u64 q0, n_pos;
+    if ((rc = reserve_batch(h, n_reads, ends[1] - ends[0], pd, q0, n_pos))) return rc;
+    pd.seq = (const unsigned char*)seq;
+    pd.qual = (const unsigned char*)qual;
+    pd.offsets = (const unsigned long long*)offsets;
+    pd.delta = 0;
+    return run_pack_and_pass(h, pd);
+  }
+  // Host input: validate offsets, then stream chunks through two staging buffers; the copy
+  // of chunk i+1 overlaps the packing and first pass of chunk i.
+  for (u64 r = 0; r < n_reads; ++r)
+    if (offsets[r + 1] < offsets[r]) return KMA_EINVAL;
+  if (offsets[n_reads] - offsets[0] + h->bases_used > h->p.max_bases) return KMA_EFULL;
+  if ((rc = setup_staging(h))) return rc;
+  u64 r0 = 0;
+  while (r0 < n_reads) {
+    u64 r1 = r0;
+    while (r1 < n_reads && offsets[r1 + 1] - offsets[r0] <= h->d.staging && r1 - r0 + 1 < h->stage_offs_cap) ++r1;
+    if (r1 == r0) return KMA_EINVAL;  // a single read longer than the staging buffer
+    const u64 nb = offsets[r1] - offsets[r0];
+    PackDesc pd;
+    u64 q0, n_pos;
+    if ((rc = reserve_batch(h, r1 - r0, nb, pd, q0, n_pos))) return rc;
+    const int b = h->stage_next;
+    h->stage_next ^= 1;
+    KMA_CUDA(cudaStreamWaitEvent(h->copy_stream, h->consumed[b], 0));
+    KMA_CUDA(cudaMemcpyAsync(h->stage_seq[b], seq + offsets[r0], nb, cudaMemcpyHostToDevice, h->copy_stream));
+    KMA_CUDA(cudaMemcpyAsync(h->stage_qual[b], qual + offsets[r0], nb, cudaMemcpyHostToDevice, h->copy_stream));
+    KMA_CUDA(cudaMemcpyAsync(h->stage_offs[b], offsets + r0, (r1 - r0 + 1) * 8, cudaMemcpyHostToDevice, h->copy_stream));
+    KMA_CUDA(cudaEventRecord(h->copied[b], h->copy_stream));
+    KMA_CUDA(cudaStreamWaitEvent(h->stream, h->copied[b], 0));
+    pd.seq = h->stage_seq[b];
+    pd.qual = h->stage_qual[b];
+    pd.offsets = h->stage_offs[b];
+    pd.delta = (long long)offsets[r0];
+    PackBatch pb;
+    std::memset(&pb, 0, offsetof(PackBatch, d) + sizeof(PackDesc));
+    pb.n = 1;
+    pb.d[0] = pd;
+    pb.total_words = n_pos / 64;
+    if ((rc = timed_launch(h, KMA_KERNEL_PACK, h->stream, true,
+                           [&] { return launch_pack(pb, h->stream, h->num_sms); })))
+      return rc;
+    KMA_CUDA(cudaEventRecord(h->consumed[b], h->stream));
+    PassBatch pb2;
+    std::memset(&pb2, 0, offsetof(PassBatch, d) + sizeof(PassDesc));
+    pb2.n = 1;
+    pb2.d[0] = pass_desc(h, h->p.use_bloom ? kModeBloom : kModeCount, q0, q0 + n_pos);
+    const u64 tile = (u64)h->shape.block_threads * h->shape.windows_per_thread;
+    pb2.total_tiles = (n_pos + tile - 1) / tile;
+    if ((rc = timed_launch(h, KMA_KERNEL_PASS, h->stream, true,
+                           [&] { return launch_pass(pb2, h->shape, h->agg, h->stream); })))
+      return rc;
+    r0 = r1;
+  }
+  // Host buffers may be reused once the call returns: wait for the copies.
+  KMA_CUDA(cudaStreamSynchronize(h->copy_stream));
+  return KMA_OK;
+}
+
+static int finalize_many(kma_handle* const* hs, uint32_t n, kma_result* out) {
+  if (!hs || n == 0 || n > KMA_MAX_BATCH) return KMA_EINVAL;
+  kma_handle* h0 = hs[0];
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!hs[i]) return KMA_EINVAL;
+    if (hs[i]->finalized || hs[i]->failed) return KMA_ESTATE;
+  }
+  // make every handle's stream work visible to h0's stream
+  std::vector<cudaEvent_t> evs;
+  for (uint32_t i = 1; i < n; ++i) {
+    if (hs[i]->stream != h0->stream) {
+      cudaEvent_t ev;
+      KMA_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      KMA_CUDA(cudaEventRecord(ev, hs[i]->stream));
+      KMA_CUDA(cudaStreamWaitEvent(h0->stream, ev, 0));
+      evs.push_back(ev);
+    }
+  }
+  for (auto ev : evs) cudaEventDestroy(ev);
+  // 1. recount pass over the Bloom handles
+  PassBatch pb;
+  std::memset(&pb, 0, sizeof(pb));
+  const u64 tile = (u64)h0->shape.block_threads * h0->shape.windows_per_thread;
+  u64 tiles = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    kma_handle* h = hs[i];
+    if (!h->p.use_bloom || h->q_used == 0) continue;
+    PassDesc d = pass_desc(h, kModeRecount, 0, h->q_used);
+    d.tile_begin = tiles;
+    tiles += (h->q_used + tile - 1) / tile;
+    pb.d[pb.n++] = d;
+  }
+  pb.total_tiles = tiles;
+  {
+    int rc = timed_launch(h0, KMA_KERNEL_RECOUNT, h0->stream, pb.n > 0 && tiles > 0,
+                          [&] { return launch_pass(pb, h0->shape, h0->agg, h0->stream); });
+    if (rc) return rc;
+  }
+  // 2. statuses -> output capacities
+  for (uint32_t i = 0; i < n; ++i) {
+    kma_handle* h = hs[i];
+    KMA_CUDA(cudaMemsetAsync(&h->status->n_out, 0, 2 * sizeof(u64), h0->stream));
+    KMA_CUDA(cudaMemcpyAsync(h->host_status, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, h0->stream));
+  }
+  KMA_CUDA(cudaStreamSynchronize(h0->stream));
+  int first_err = KMA_OK;
+  std::vector<int> ok(n, 0);
+  for (uint32_t i = 0; i < n; ++i) {
+    kma_handle* h = hs[i];
+    int rc = flags_to_code(h->host_status->flags);
+    if (rc) { h->failed = true; if (!first_err) first_err = rc; continue; }
+    cudaStream_t saved = h->stream;
+    h->stream = h0->stream;
+    rc = ensure_output(h, h->host_status->table_keys);
+    h->stream = saved;
+    if (rc) { h->failed = true; if (!first_err) first_err = rc; continue; }
+    ok[i] = 1;
+  }
+  // 3. classify + compact
+  ClassBatch cb;
+  std::memset(&cb, 0, sizeof(cb));
+  cb.write = 1;
+  u64 blocks = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!ok[i]) continue;
+    ClassDesc c = class_desc(hs[i]);
+    c.block_begin = blocks;
+    blocks += (c.slots + kClassTile - 1) / kClassTile;
+    cb.d[cb.n++] = c;
+  }
+  cb.total_blocks = blocks;
+  {
+    int rc = timed_launch(h0, KMA_KERNEL_CLASSIFY, h0->stream, cb.n > 0 && blocks > 0,
+                          [&] { return launch_classify(cb, h0->stream, h0->num_sms); });
+    if (rc) return rc;
+  }
+  for (uint32_t i = 0; i < n; ++i)
+    if (ok[i]) KMA_CUDA(cudaMemcpyAsync(hs[i]->host_status, hs[i]->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, h0->stream));
+  KMA_CUDA(cudaStreamSynchronize(h0->stream));
+  for (uint32_t i = 0; i < n; ++i) {
+    kma_handle* h = hs[i];
+    if (!ok[i]) { if (out) std::memset(&out[i], 0, sizeof(kma_result)); continue; }
+    int rc = flags_to_code(h->host_status->flags);
+    if (rc) { h->failed = true; if (!first_err) first_err = rc; if (out) std::memset(&out[i], 0, sizeof(kma_result)); continue; }
+    fill_result(h);
+    h->finalized = true;
+    if (out) out[i] = h->res;
+  }
+  return first_err;
+}
+
+int kmer_analysis_finalize(kma_handle* h, kma_result* out) {
+  if (!h) return KMA_EINVAL;
+  kma_handle* hs[1] = {h};
+  return finalize_many(hs, 1, out);
+}
+
+int kmer_analysis_finalize_batch(kma_handle* const* hs, uint32_t n, kma_result* out) {
+  return finalize_many(hs, n, out);
+}
+
+int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uint32_t n) {
+  if (!hs || !reads || n == 0 || n > KMA_MAX_BATCH) return KMA_EINVAL;
+  kma_handle* h0 = hs[0];
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!hs[i]) return KMA_EINVAL;
+    if (hs[i]->finalized || hs[i]->failed) return KMA_ESTATE;
+    if (hs[i]->device != h0->device) return KMA_EINVAL;
+    for (uint32_t j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return KMA_EINVAL;
+    if (reads[i].n_reads && (!reads[i].seq || !reads[i].qual || !reads[i].offsets)) return KMA_EINVAL;
+  }
+  PackBatch pk;
+  std::memset(&pk, 0, sizeof(pk));
+  PassBatch ps;
+  std::memset(&ps, 0, sizeof(ps));
+  const u64 tile = (u64)h0->shape.block_threads * h0->shape.windows_per_thread;
+  u64 words = 0, tiles = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    kma_handle* h = hs[i];
+    if (reads[i].n_reads == 0) continue;
+    PackDesc pd;
+    u64 q0, n_pos;
+    int rc = reserve_batch(h, reads[i].n_reads, reads[i].n_bases, pd, q0, n_pos);
+    if (rc) return rc;
+    pd.seq = (const unsigned char*)reads[i].seq;
+    pd.qual = (const unsigned char*)reads[i].qual;
+    pd.offsets = (const unsigned long long*)reads[i].offsets;
+    pd.delta = 0;
+    pd.word_begin = words;
+    words += n_pos / 64;
+    pk.d[pk.n++] = pd;
+    PassDesc d = pass_desc(h, h->p.use_bloom ? kModeBloom : kModeCount, q0, q0 + n_pos);
+    d.tile_begin = tiles;
+    tiles += (n_pos + tile - 1) / tile;
+    ps.d[ps.n++] = d;
+  }
+  pk.total_words = words;
+  ps.total_tiles = tiles;
+  int rc = timed_launch(h0, KMA_KERNEL_PACK, h0->stream, pk.n > 0 && words > 0,
+                        [&] { return launch_pack(pk, h0->stream, h0->num_sms); });
+  if (rc) return rc;
+  return timed_launch(h0, KMA_KERNEL_PASS, h0->stream, ps.n > 0 && tiles > 0,
+                      [&] { return launch_pass(ps, h0->shape, h0->agg, h0->stream); });
+}
+
+int kmer_analysis_copy_result(kma_handle* h, uint64_t* keys, uint32_t* counts, uint32_t* ext,
+                              uint8_t* codes, uint64_t capacity, int on_device) {
+  if (!h) return KMA_EINVAL;
+  if (!h->finalized) return KMA_ESTATE;
+  const u64 n = h->res.n;
+  if (capacity < n) return KMA_EINVAL;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (n) {
+    if (keys) KMA_CUDA(cudaMemcpyAsync(keys, h->out_keys, n * 16, kind, h->stream));
+    if (counts) KMA_CUDA(cudaMemcpyAsync(counts, h->out_counts, n * 4, kind, h->stream));
+    if (ext) KMA_CUDA(cudaMemcpyAsync(ext, h->out_ext, n * 32, kind, h->stream));
+    if (codes) KMA_CUDA(cudaMemcpyAsync(codes, h->out_codes, n * 2, kind, h->stream));
+  }
+  KMA_CUDA(cudaStreamSynchronize(h->stream));
+  return KMA_OK;
+}
+
+int kmer_analysis_query(kma_handle* h, const uint64_t* keys, uint64_t n, uint32_t* counts,
+                        uint32_t* ext, uint8_t* codes, int on_device) {
+  if (!h) return KMA_EINVAL;
+  if (!h->finalized) return KMA_ESTATE;
+  if (n == 0) return KMA_OK;
+  if (!keys || !counts || !ext || !codes) return KMA_EINVAL;
+  const unsigned min_ext = h->p.min_ext_count ? h->p.min_ext_count : 1;
+  if (on_device) {
+    return timed_launch(h, KMA_KERNEL_QUERY, h->stream, true, [&] {
+      return launch_query(h->table, h->d.plan.table_slots, h->p.k, h->p.canonical, h->p.min_depth,
+                          min_ext, (const u64*)keys, n, counts, ext, codes, h->status, h->stream);
+    });
+  }
+  u64* dk = nullptr;
+  unsigned *dc = nullptr, *de = nullptr;
+  unsigned char* dcode = nullptr;
+  int rc;
+  if ((rc = dalloc(h, &dk, 2 * n)) || (rc = dalloc(h, &dc, n)) || (rc = dalloc(h, &de, 8 * n)) ||
+      (rc = dalloc(h, &dcode, 2 * n))) {
+    dfree(h, dk); dfree(h, dc); dfree(h, de); dfree(h, dcode);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(dk, keys, n * 16, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    rc = timed_launch(h, KMA_KERNEL_QUERY, h->stream, true, [&] {
+      return launch_query(h->table, h->d.plan.table_slots, h->p.k, h->p.canonical, h->p.min_depth,
+                          min_ext, dk, n, dc, de, dcode, h->status, h->stream);
+    });
+    if (rc) { dfree(h, dk); dfree(h, dc); dfree(h, de); dfree(h, dcode); return rc; }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(counts, dc, n * 4, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ext, de, n * 32, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(codes, dcode, n * 2, cudaMemcpyDeviceToHost, h->stream);
+  dfree(h, dk); dfree(h, dc); dfree(h, de); dfree(h, dcode);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "query");
+  return KMA_OK;
+}
+
+int kmer_analysis_reset(kma_handle* h) {
+  if (!h) return KMA_EINVAL;
+  return clear_state(h);
+}
+
+int kmer_analysis_set_stream(kma_handle* h, void* cuda_stream) {
+  if (!h) return KMA_EINVAL;
+  h->stream = (cudaStream_t)cuda_stream;
+  return KMA_OK;
+}
+
+int kmer_analysis_status(kma_handle* h) {
+  if (!h) return KMA_EINVAL;
+  int rc = read_status(h);
+  if (rc) return rc;
+  return flags_to_code(h->host_status->flags);
+}
+
+uint64_t kmer_analysis_device_bytes(const kma_handle* h) {
+  if (!h) return 0;
+  return h->d.plan.device_bytes + h->out_cap * (16 + 4 + 32 + 2);
+}
+
+int kmer_analysis_set_profiling(kma_handle* h, int enable) {
+  if (!h) return KMA_EINVAL;
+  h->profiling = enable != 0;
+  return KMA_OK;
+}
+
+int kmer_analysis_timings(kma_handle* h, kma_timings* out, int reset) {
+  if (!h || !out) return KMA_EINVAL;
+  KMA_CUDA(cudaStreamSynchronize(h->stream));
+  for (auto& r : h->prof) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess && r.kind >= 0 && r.kind < 8) h->ms[r.kind] += ms;
+    h->event_pool.push_back(r.a);
+    h->event_pool.push_back(r.b);
+  }
+  h->prof.clear();
+  cudaGetLastError();
+  std::memset(out, 0, sizeof(*out));
+  for (int i = 0; i < 8; ++i) {
+    out->ms[i] = h->ms[i];
+    out->launches[i] = h->launches[i];
+    out->total_launches += h->launches[i];
+  }
+  int rc = read_status(h);
+  if (rc) return rc;
+  out->first_sightings = h->host_status->first_sightings;
+  if (reset) {
+    for (int i = 0; i < 8; ++i) { h->ms[i] = 0; h->launches[i] = 0; }
+  }
+  return KMA_OK;
+}
+
+void kmer_analysis_destroy(kma_handle* h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+const char* kmer_analysis_strerror(int code) {
+  switch (code) {
+    case KMA_OK: return "ok";
+    case KMA_EINVAL: return "invalid argument";
+    case KMA_ENOMEM: return "out of device memory";
+    case KMA_EFULL: return "capacity exceeded (hash table or read arena)";
+    case KMA_ESTATE: return "call not allowed in this state";
+    case KMA_ETIMEOUT: return "device wait timed out";
+    case KMA_EOVERFLOW: return "k-mer counter overflow";
+    case KMA_ECUDA: return g_last_cuda_error.empty() ? "CUDA error" : g_last_cuda_error.c_str();
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

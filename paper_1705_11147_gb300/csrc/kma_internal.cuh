@@ -1,0 +1,150 @@
+// Internal layout shared by the library's CUDA translation units (not part of the C ABI).
+//
+// Device data of one handle ("sample"):
+//   packed-read arena  positions q = 0 .. arena_positions-1. Each count() batch starts at a
+//                      multiple of 64; read r of a batch occupies [ps_r, ps_r + len_r) and is
+//                      followed by one separator position (invalid), so no window can span
+//                      two reads and the bases before/after a read are never usable.
+//     codes  u64[arena/32]  2 bits per position, first position in the two most significant
+//                           bits (A0 C1 G2 T3; 0 for invalid positions)
+//     inv    u64[arena/64]  1 = position is not A/C/G/T (separator, N, padding), MSB first
+//     hq     u64[arena/64]  1 = A/C/G/T with Phred >= qual_threshold, MSB first
+//     marks  u32[arena/32]  Bloom pass: 1 = this window was the first sighting of its k-mer
+//   bloom    u64[bloom_words]  blocked Bloom filter: all bits of a k-mer in one word
+//   table    Slot[slots]       open addressing, linear probing, 64-byte slots
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kma {
+
+constexpr uint64_t kEmpty = ~0ull;          // both key words of an empty slot
+constexpr uint32_t kMaxProbe = 1u << 14;    // probe limit before reporting a full table
+constexpr int kMaxBatch = 64;
+
+// Status flags raised on the device.
+constexpr uint32_t kFlagFull = 1u;
+constexpr uint32_t kFlagOverflow = 2u;
+constexpr uint32_t kFlagBadOffsets = 4u;
+
+// One hash-table slot: the key and count share the first 32-byte sector, the eight
+// extension counters fill the second, so an update touches one half cache line.
+struct __align__(64) Slot {
+  unsigned long long lo, hi;
+  unsigned int count;
+  unsigned int pad[3];
+  unsigned int ext[8];  // left A C G T, right A C G T
+};
+static_assert(sizeof(Slot) == 64, "slot must be 64 bytes");
+
+struct DevStatus {
+  unsigned int flags;
+  unsigned int pad;
+  unsigned long long valid_windows;
+  unsigned long long table_keys;
+  unsigned long long n_out;
+  unsigned long long n_uu;
+  unsigned long long first_sightings;  // Bloom pass: windows marked as first sightings
+  unsigned long long reserved[2];
+};
+
+// Per-sample view the pass kernels need. Passed by value inside kernel parameters.
+struct PassDesc {
+  const unsigned long long* codes;
+  const unsigned long long* inv;
+  const unsigned long long* hq;
+  unsigned int* marks;
+  unsigned long long* bloom;
+  Slot* table;
+  DevStatus* status;
+  unsigned long long bloom_words;
+  unsigned long long slots;
+  unsigned long long q0;          // first window start of this launch (multiple of 64)
+  unsigned long long q1;          // one past the last window start
+  unsigned long long tile_begin;  // first global tile index of this sample
+  unsigned int k;
+  unsigned int bloom_h;
+  unsigned int canonical;
+  unsigned int mode;              // kModeBloom / kModeCount / kModeRecount
+  unsigned int n_parts;           // owner-computes partition: count only keys owned by `part`
+  unsigned int part;
+};
+
+struct PassBatch {
+  unsigned int n;
+  unsigned int pad;
+  unsigned long long total_tiles;
+  PassDesc d[kMaxBatch];
+};
+
+constexpr unsigned int kModeBloom = 0;    // Bloom test-and-set; "seen" -> insert + count; else mark
+constexpr unsigned int kModeCount = 1;    // no Bloom: insert + count every window
+constexpr unsigned int kModeRecount = 2;  // marked windows: count if the key is in the table
+
+// Pack kernel per-sample input.
+struct PackDesc {
+  const unsigned char* seq;
+  const unsigned char* qual;
+  const unsigned long long* offsets;  // n_reads + 1 entries
+  long long delta;                    // seq/qual index of base b is offsets-relative b - delta
+  unsigned long long n_reads;
+  unsigned long long n_bases;         // offsets[n_reads] - offsets[0] as the host believes
+  unsigned long long q0;              // arena start (multiple of 64)
+  unsigned long long n_pos;           // n_bases + n_reads, rounded up to a multiple of 64
+  unsigned long long word_begin;      // prefix of 64-position words over the batch
+  unsigned long long* codes;
+  unsigned long long* inv;
+  unsigned long long* hq;
+  DevStatus* status;
+  unsigned int qual_min;              // qual byte >= qual_min <=> Phred >= threshold
+  unsigned int pad;
+};
+
+struct PackBatch {
+  unsigned int n;
+  unsigned int pad;
+  unsigned long long total_words;
+  PackDesc d[kMaxBatch];
+};
+
+struct ClassDesc {
+  const Slot* table;
+  DevStatus* status;
+  unsigned long long slots;
+  unsigned long long* out_keys;
+  unsigned int* out_counts;
+  unsigned int* out_ext;
+  unsigned char* out_codes;
+  unsigned long long out_cap;
+  unsigned long long block_begin;
+  unsigned int min_depth;
+  unsigned int min_ext;
+};
+
+struct ClassBatch {
+  unsigned int n;
+  unsigned int write;   // 0: count survivors only; 1: compact into out_*
+  unsigned long long total_blocks;
+  ClassDesc d[kMaxBatch];
+};
+
+struct LaunchShape {
+  int block_threads;
+  int windows_per_thread;
+  int grid;
+};
+
+// Launchers (kma_kernels.cu). All enqueue on `stream`.
+cudaError_t launch_pack(const PackBatch& b, cudaStream_t stream, int num_sms);
+cudaError_t launch_pass(const PassBatch& b, const LaunchShape& shape, bool warp_aggregate,
+                        cudaStream_t stream);
+cudaError_t launch_classify(const ClassBatch& b, cudaStream_t stream, int num_sms);
+cudaError_t launch_table_init(Slot* table, unsigned long long slots, cudaStream_t stream);
+cudaError_t launch_query(const Slot* table, unsigned long long slots, unsigned int k,
+                         unsigned int canonical, unsigned int min_depth, unsigned int min_ext,
+                         const unsigned long long* keys, unsigned long long n,
+                         unsigned int* counts, unsigned int* ext, unsigned char* codes,
+                         DevStatus* status, cudaStream_t stream);
+int pass_max_ctas_per_sm(int block_threads, int windows_per_thread, bool warp_aggregate);
+
+}  // namespace kma

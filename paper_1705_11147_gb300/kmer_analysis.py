@@ -1,0 +1,272 @@
+"""Python binding of the k-mer analysis library: the C ABI's calls under the same names,
+taking numpy arrays (host) or torch CUDA tensors (device) and marshalling pointers.
+PyTorch is used only for device memory and streams; all of the work runs in the library's
+CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import capi
+from .capi import check
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_cuda_tensor(x) -> bool:
+    try:
+        torch = _torch()
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        try:
+            torch = _torch()
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:  # pragma: no cover
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_params(k: int, max_bases: int, min_depth: int = 2, min_ext_count: int = 2,
+                qual_threshold: int = 20, qual_offset: int = 33, use_bloom: bool = True,
+                canonical: bool = True, max_reads: int = 0, expected_distinct: int = 0,
+                bloom_fpr: float = 0.01, table_capacity: int = 0, expected_keys: int = 0,
+                load_factor: float = 0.0, staging_bytes: int = 0, block_threads: int = 0,
+                windows_per_thread: int = 0, ctas_per_sm: int = 0,
+                warp_aggregate: bool = False, n_parts: int = 1, part: int = 0) -> capi.kma_params:
+    return capi.kma_params(k, min_depth, min_ext_count, qual_threshold, qual_offset,
+                           int(bool(use_bloom)), int(bool(canonical)), max_bases, max_reads,
+                           expected_distinct, bloom_fpr, table_capacity, expected_keys,
+                           load_factor, staging_bytes, block_threads, windows_per_thread,
+                           ctas_per_sm, int(bool(warp_aggregate)), n_parts, part)
+
+
+def plan(params: capi.kma_params) -> capi.kma_plan:
+    """kmer_analysis_plan: sizes a handle with `params` would have (host only)."""
+    out = capi.kma_plan()
+    check(capi.load().kmer_analysis_plan(ctypes.byref(params), ctypes.byref(out)), "plan")
+    return out
+
+
+@dataclass
+class Result:
+    """Finalized records (order unspecified; see `sorted()`)."""
+    keys: np.ndarray      # uint64[n, 2] (lo, hi)
+    counts: np.ndarray    # uint32[n]
+    ext: np.ndarray       # uint32[n, 8] left A C G T, right A C G T
+    codes: np.ndarray     # uint8[n, 2]  0..3 A C G T, 4 X, 5 F
+    n_uu: int = 0
+    valid_windows: int = 0
+    table_keys: int = 0
+    meta: dict = field(default_factory=dict)
+
+    def __len__(self):
+        return int(self.counts.shape[0])
+
+    def sorted(self) -> "Result":
+        order = np.lexsort((self.keys[:, 0], self.keys[:, 1]))
+        return Result(self.keys[order], self.counts[order], self.ext[order], self.codes[order],
+                      self.n_uu, self.valid_windows, self.table_keys, dict(self.meta))
+
+
+class KmerAnalysis:
+    """One handle: kmer_analysis_create / count / finalize / copy_result / query / reset /
+    destroy. Inputs are numpy arrays (host) or torch CUDA tensors (device)."""
+
+    def __init__(self, params: capi.kma_params | None = None, stream=None, **kw):
+        self._lib = capi.load()
+        self.params = params if params is not None else make_params(**kw)
+        self._h = ctypes.c_void_p()
+        self._stream = _stream_handle(stream)
+        check(self._lib.kmer_analysis_create(ctypes.byref(self.params), self._stream,
+                                             ctypes.byref(self._h)), "create")
+        self.result_info: capi.kma_result | None = None
+
+    # -------------------------------------------------------------- C ABI calls
+    @property
+    def handle(self):
+        return self._h
+
+    def count(self, seq, qual, offsets) -> None:
+        if _is_cuda_tensor(seq):
+            assert _is_cuda_tensor(qual) and _is_cuda_tensor(offsets)
+            n_reads = offsets.numel() - 1
+            check(self._lib.kmer_analysis_count(self._h, seq.data_ptr(), qual.data_ptr(),
+                                                offsets.data_ptr(), n_reads, 1), "count")
+            return
+        seq = np.ascontiguousarray(seq, dtype=np.uint8)
+        qual = np.ascontiguousarray(qual, dtype=np.uint8)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        check(self._lib.kmer_analysis_count(self._h, seq.ctypes.data, qual.ctypes.data,
+                                            offsets.ctypes.data, offsets.shape[0] - 1, 0), "count")
+
+    def finalize(self) -> capi.kma_result:
+        r = capi.kma_result()
+        check(self._lib.kmer_analysis_finalize(self._h, ctypes.byref(r)), "finalize")
+        self.result_info = r
+        return r
+
+    def copy_result(self) -> Result:
+        r = self.result_info
+        if r is None:
+            raise RuntimeError("finalize() first")
+        n = int(r.n)
+        keys = np.zeros((n, 2), np.uint64)
+        counts = np.zeros(n, np.uint32)
+        ext = np.zeros((n, 8), np.uint32)
+        codes = np.zeros((n, 2), np.uint8)
+        check(self._lib.kmer_analysis_copy_result(self._h, keys.ctypes.data, counts.ctypes.data,
+                                                  ext.ctypes.data, codes.ctypes.data, n, 0),
+              "copy_result")
+        return Result(keys, counts, ext, codes, int(r.n_uu), int(r.valid_windows), int(r.table_keys))
+
+    def copy_result_device(self):
+        """Result arrays as torch CUDA tensors (copies of the handle-owned buffers)."""
+        torch = _torch()
+        r = self.result_info
+        n = int(r.n)
+        keys = torch.empty((n, 2), dtype=torch.int64, device="cuda")
+        counts = torch.empty(n, dtype=torch.int32, device="cuda")
+        ext = torch.empty((n, 8), dtype=torch.int32, device="cuda")
+        codes = torch.empty((n, 2), dtype=torch.uint8, device="cuda")
+        check(self._lib.kmer_analysis_copy_result(self._h, keys.data_ptr(), counts.data_ptr(),
+                                                  ext.data_ptr(), codes.data_ptr(), n, 1),
+              "copy_result")
+        return keys, counts, ext, codes
+
+    def query(self, keys, out=None):
+        """Look up k-mers keys[n, 2] (either orientation). numpy in -> numpy out (synchronous);
+        CUDA tensor in -> CUDA tensors out (enqueued on the handle's stream)."""
+        if _is_cuda_tensor(keys):
+            torch = _torch()
+            n = keys.shape[0]
+            counts, ext, codes = out if out is not None else (
+                torch.empty(n, dtype=torch.int32, device=keys.device),
+                torch.empty((n, 8), dtype=torch.int32, device=keys.device),
+                torch.empty((n, 2), dtype=torch.uint8, device=keys.device))
+            check(self._lib.kmer_analysis_query(self._h, keys.data_ptr(), n, counts.data_ptr(),
+                                                ext.data_ptr(), codes.data_ptr(), 1), "query")
+            return counts, ext, codes
+        q = np.ascontiguousarray(keys, dtype=np.uint64).reshape(-1, 2)
+        n = q.shape[0]
+        counts = np.zeros(n, np.uint32)
+        ext = np.zeros((n, 8), np.uint32)
+        codes = np.zeros((n, 2), np.uint8)
+        check(self._lib.kmer_analysis_query(self._h, q.ctypes.data, n, counts.ctypes.data,
+                                            ext.ctypes.data, codes.ctypes.data, 0), "query")
+        return counts, ext, codes
+
+    def reset(self) -> None:
+        check(self._lib.kmer_analysis_reset(self._h), "reset")
+        self.result_info = None
+
+    def set_stream(self, stream) -> None:
+        self._stream = _stream_handle(stream)
+        check(self._lib.kmer_analysis_set_stream(self._h, self._stream), "set_stream")
+
+    def status(self) -> int:
+        return int(self._lib.kmer_analysis_status(self._h))
+
+    def set_profiling(self, enable: bool = True) -> None:
+        check(self._lib.kmer_analysis_set_profiling(self._h, int(bool(enable))), "set_profiling")
+
+    def timings(self, reset: bool = False) -> dict:
+        t = capi.kma_timings()
+        check(self._lib.kmer_analysis_timings(self._h, ctypes.byref(t), int(bool(reset))), "timings")
+        out = {f"ms_{k}": float(t.ms[i]) for i, k in enumerate(capi.KERNEL_KINDS)}
+        out.update({f"n_{k}": int(t.launches[i]) for i, k in enumerate(capi.KERNEL_KINDS)})
+        out["launches"] = int(t.total_launches)
+        out["first_sightings"] = int(t.first_sightings)
+        return out
+
+    def device_bytes(self) -> int:
+        return int(self._lib.kmer_analysis_device_bytes(self._h))
+
+    def destroy(self) -> None:
+        if self._h:
+            self._lib.kmer_analysis_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    close = destroy
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+
+def count_batch(handles: list[KmerAnalysis], reads: list[tuple]) -> None:
+    """kmer_analysis_count_batch: reads[i] = (seq, qual, offsets) CUDA tensors for handle i.
+    Enqueued on handles[0]'s stream; does not synchronise."""
+    n = len(handles)
+    assert 0 < n <= capi.KMA_MAX_BATCH and len(reads) == n
+    hs = (ctypes.c_void_p * n)(*[h.handle.value for h in handles])
+    arr = (capi.kma_reads * n)()
+    for i, (seq, qual, offs) in enumerate(reads):
+        arr[i] = capi.kma_reads(seq.data_ptr(), qual.data_ptr(), offs.data_ptr(),
+                                offs.numel() - 1, seq.numel())
+    check(capi.load().kmer_analysis_count_batch(hs, arr, n), "count_batch")
+
+
+def finalize_batch(handles: list[KmerAnalysis]) -> list[capi.kma_result]:
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.handle.value for h in handles])
+    out = (capi.kma_result * n)()
+    rc = capi.load().kmer_analysis_finalize_batch(hs, n, out)
+    for i, h in enumerate(handles):
+        h.result_info = out[i]
+    check(rc, "finalize_batch")
+    return list(out)
+
+
+def count_kmers(seq, qual, offsets, k: int, min_depth: int = 2, min_ext_count: int = 2,
+                qual_threshold: int = 20, use_bloom: bool = True, canonical: bool = True,
+                expected_distinct: int = 0, expected_keys: int = 0, stream=None,
+                retries: int = 4, **kw) -> Result:
+    """One-shot convenience: create -> count -> finalize -> copy_result -> destroy.
+    A full table (KMA_EFULL) is retried with twice the capacity; results never depend on the
+    capacity."""
+    n_bases = int(offsets[-1] - offsets[0]) if not _is_cuda_tensor(offsets) else int(seq.numel())
+    n_reads = int(offsets.shape[0] - 1)
+    table_capacity = kw.pop("table_capacity", 0)
+    for attempt in range(retries + 1):
+        p = make_params(k=k, max_bases=max(n_bases, 1), max_reads=max(n_reads, 1),
+                        min_depth=min_depth, min_ext_count=min_ext_count,
+                        qual_threshold=qual_threshold, use_bloom=use_bloom, canonical=canonical,
+                        expected_distinct=expected_distinct, expected_keys=expected_keys,
+                        table_capacity=table_capacity, **kw)
+        ka = KmerAnalysis(p, stream=stream)
+        try:
+            ka.count(seq, qual, offsets)
+            ka.finalize()
+            res = ka.copy_result()
+            res.meta["table_slots"] = plan(p).table_slots
+            return res
+        except capi.KmaError as e:
+            if e.code != capi.KMA_EFULL or attempt == retries:
+                raise
+            table_capacity = 2 * plan(p).table_slots
+        finally:
+            ka.destroy()
+    raise AssertionError("unreachable")

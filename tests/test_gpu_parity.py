@@ -1,0 +1,297 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, record by record.
+
+Every comparison is bit-exact (integer work): same k-mer set, counts, eight extension
+counters and two side codes per k-mer, after sorting both by key (record order is
+unspecified on the GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_11147_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    return torch
+
+
+def to_dev(torch, rs):
+    return (torch.from_numpy(rs.seq).cuda(), torch.from_numpy(rs.qual).cuda(),
+            torch.from_numpy(rs.offsets.astype(np.int64)).cuda())
+
+
+def run_gpu(torch, rs, device_inputs=True, batches=1, **kw):
+    from paper_1705_11147_gb300 import KmerAnalysis, make_params
+    p = dict(rs.meta.get("params", {}))
+    p.pop("bloom_fpr", None)
+    p.update(kw)
+    p.setdefault("max_bases", max(rs.n_bases, 1))
+    p.setdefault("max_reads", max(rs.n_reads, 1))
+    p.setdefault("expected_distinct", max(rs.n_bases, 1))
+    with KmerAnalysis(make_params(**p)) as ka:
+        cuts = np.linspace(0, rs.n_reads, batches + 1).astype(np.int64)
+        for b in range(batches):
+            r0, r1 = int(cuts[b]), int(cuts[b + 1])
+            offs = rs.offsets[r0:r1 + 1]
+            if device_inputs:
+                seq, qual, o = to_dev(torch, rs)
+                ka.count(seq, qual, torch.from_numpy(offs.astype(np.int64)).cuda())
+            else:
+                ka.count(rs.seq, rs.qual, offs)
+        ka.finalize()
+        return ka.copy_result().sorted()
+
+
+def assert_same(got, want, what=""):
+    assert len(got) == len(want), f"{what}: {len(got)} vs {len(want)} records"
+    for f in ("keys", "counts", "ext", "codes"):
+        a, b = getattr(got, f), getattr(want, f)
+        if not np.array_equal(a, b):
+            bad = np.nonzero((a != b).reshape(a.shape[0], -1).any(1))[0][:5]
+            raise AssertionError(f"{what}: field {f} differs at rows {bad}: {a[bad]} vs {b[bad]}")
+
+
+def oracle_for(rs, **kw):
+    p = dict(rs.meta.get("params", {}))
+    p.pop("bloom_fpr", None)
+    for key in ("use_bloom", "load_factor", "table_capacity", "block_threads", "windows_per_thread",
+                "warp_aggregate", "ctas_per_sm", "expected_distinct", "expected_keys", "staging_bytes",
+                "max_bases", "max_reads", "bloom_fpr"):
+        kw.pop(key, None)
+    p.update(kw)
+    return oracle.run(rs.seq, rs.qual, rs.offsets, **p)
+
+
+def readset(reads, quals=None, **params):
+    seq, qual, offs = oracle.reads_from_strings(reads, quals)
+    rs = synth.ReadSet(seq, qual, offs)
+    rs.meta["params"] = params
+    return rs
+
+
+# ------------------------------------------------------------------ paper examples
+
+def test_chopping_example(gpu):
+    rs = readset(["GATCTGAACCG"], k=3, min_depth=1, min_ext_count=1, canonical=False, use_bloom=False)
+    got = run_gpu(gpu, rs)
+    assert oracle.unpack(got.keys, 3) == sorted(["GAT", "ATC", "TCT", "CTG", "TGA", "GAA", "AAC", "ACC", "CCG"])
+    assert got.valid_windows == 9
+    rs.meta["params"]["canonical"] = True
+    assert_same(run_gpu(gpu, rs), oracle_for(rs), "canonical example")
+
+
+def test_contig_and_fork_examples(gpu):
+    rs = readset(["GATCTGA", "GATCTGA"], k=3, min_depth=2, min_ext_count=2, canonical=False)
+    got = run_gpu(gpu, rs)
+    i = oracle.unpack(got.keys, 3).index("CTG")
+    assert tuple(got.codes[i]) == (3, 0)  # left T, right A: value "AT" as [right][left]
+    rs = readset(["GAAC", "GAAC", "GAAT", "GAAT"], k=3, min_depth=2, min_ext_count=2, canonical=False)
+    got = run_gpu(gpu, rs)
+    i = oracle.unpack(got.keys, 3).index("GAA")
+    assert tuple(got.codes[i]) == (4, 5) and got.counts[i] == 4
+
+
+# ------------------------------------------------------------------ tiny random / edge cases
+
+@pytest.mark.parametrize("k", [1, 3, 5, 7, 21, 31, 33, 51, 63])
+def test_random_reads_all_k(gpu, k):
+    rs = synth.random_reads(seed=77 + k, n_reads=3000, min_len=0, max_len=200,
+                            alphabet=b"ACGTACGTACGTACGTacgtNRY", q_lo=10, q_hi=30)
+    for bloom, md in [(False, 1), (False, 2), (True, 2), (True, 3)]:
+        for canonical in (True, False):
+            if canonical and k % 2 == 0:
+                continue
+            params = dict(k=k, min_depth=md, min_ext_count=2, qual_threshold=20, canonical=canonical)
+            rs.meta["params"] = params
+            got = run_gpu(gpu, rs, use_bloom=bloom)
+            assert_same(got, oracle_for(rs), f"k={k} bloom={bloom} md={md} canonical={canonical}")
+
+
+def test_low_complexity_and_repeats(gpu):
+    # the same k-mer many times inside one warp's windows (homopolymers, dinucleotide runs)
+    reads = ["A" * 300, "AC" * 150, "ACGT" * 75, "GATTACA" * 40, "T" * 70 + "G" + "T" * 70] * 40
+    quals = ["I" * len(r) for r in reads]
+    for k in (3, 21, 31, 51):
+        rs = readset(reads, quals, k=k, min_depth=2, min_ext_count=2, qual_threshold=20)
+        want = oracle_for(rs)
+        for agg in (False, True):
+            for bloom in (False, True):
+                assert_same(run_gpu(gpu, rs, warp_aggregate=agg, use_bloom=bloom), want,
+                            f"k={k} agg={agg} bloom={bloom}")
+
+
+def test_edge_inputs(gpu):
+    # no reads with windows: empty reads, reads shorter than k, all-N reads
+    rs = readset(["", "ACG", "NNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNN", ""],
+                 k=31, min_depth=2, min_ext_count=2, qual_threshold=20)
+    got = run_gpu(gpu, rs)
+    assert len(got) == 0 and got.valid_windows == 0
+    # a single read of exactly k bases, twice
+    r = "ACGT" * 15 + "ACG"
+    rs = readset([r, r], k=63, min_depth=2, min_ext_count=1)
+    got = run_gpu(gpu, rs)
+    assert_same(got, oracle_for(rs), "k=63 single window")
+    assert got.counts.tolist() == [2]
+
+
+# ------------------------------------------------------------------ workloads
+
+@pytest.fixture(scope="module")
+def plain(gpu):
+    rs = synth.workload("plain_1m")
+    return rs, oracle.run_readset(rs)
+
+
+def test_plain_1m_full(gpu, plain):
+    rs, want = plain
+    got = run_gpu(gpu, rs, use_bloom=True)
+    assert_same(got, want, "plain_1m bloom")
+    assert got.valid_windows == want.valid_windows
+    assert got.n_uu == int(want.uu_mask().sum())
+
+
+def test_plain_1m_without_bloom(gpu, plain):
+    rs, want = plain
+    assert_same(run_gpu(gpu, rs, use_bloom=False), want, "plain_1m no bloom")
+
+
+def test_host_inputs_chunked(gpu, plain):
+    rs, want = plain
+    got = run_gpu(gpu, rs, device_inputs=False, staging_bytes=1 << 20)  # ~30 chunks
+    assert_same(got, want, "host inputs")
+
+
+def test_multiple_count_calls(gpu, plain):
+    rs, want = plain
+    assert_same(run_gpu(gpu, rs, batches=5), want, "5 count() calls")
+
+
+@pytest.mark.parametrize("shape", [
+    dict(block_threads=128, windows_per_thread=1),
+    dict(block_threads=256, windows_per_thread=8, warp_aggregate=True),
+    dict(block_threads=1024, windows_per_thread=2, ctas_per_sm=1),
+    dict(block_threads=512, windows_per_thread=16, load_factor=0.85),
+    dict(expected_distinct=50_000, bloom_fpr=0.3),       # tiny, saturated Bloom filter
+    dict(expected_distinct=200_000_000, bloom_fpr=0.001),  # huge filter
+])
+def test_results_independent_of_tuning(gpu, plain, shape):
+    rs, want = plain
+    assert_same(run_gpu(gpu, rs, **shape), want, str(shape))
+
+
+def test_bacterial_5m_full(gpu):
+    rs = synth.workload("bacterial_5m")
+    want = oracle.run_readset(rs)
+    got = run_gpu(gpu, rs, expected_distinct=80_000_000, expected_keys=20_000_000)
+    assert_same(got, want, "bacterial_5m")
+    assert got.valid_windows == want.valid_windows
+
+
+def test_table_full_is_reported(gpu, plain):
+    from paper_1705_11147_gb300 import KMA_EFULL, KmaError, count_kmers
+    rs, want = plain
+    with pytest.raises(KmaError) as ei:
+        run_gpu(gpu, rs, table_capacity=100_000)
+    assert ei.value.code == KMA_EFULL
+    # the convenience wrapper retries with a larger table; the result does not depend on it
+    got = count_kmers(rs.seq, rs.qual, rs.offsets, k=31, table_capacity=300_000,
+                      expected_distinct=rs.n_bases).sorted()
+    assert_same(got, want, "after EFULL retry")
+
+
+def test_reset_and_reuse(gpu, plain):
+    from paper_1705_11147_gb300 import KmerAnalysis, make_params
+    rs, want = plain
+    small = synth.workload("plain_1m", scale=0.1)
+    seq, qual, offs = to_dev(gpu, rs)
+    with KmerAnalysis(make_params(k=31, max_bases=rs.n_bases, max_reads=rs.n_reads,
+                                  expected_distinct=rs.n_bases)) as ka:
+        for rep in range(2):
+            s2, q2, o2 = to_dev(gpu, small)
+            ka.count(s2, q2, o2)
+            ka.finalize()
+            assert_same(ka.copy_result().sorted(), oracle.run_readset(small), "small")
+            ka.reset()
+            ka.count(seq, qual, offs)
+            ka.finalize()
+            assert_same(ka.copy_result().sorted(), want, f"rep {rep}")
+            ka.reset()
+
+
+def test_query_matches_oracle(gpu):
+    from paper_1705_11147_gb300 import KmerAnalysis, make_params
+    rs = synth.workload("bacterial_5m", scale=0.05)
+    want = oracle.run_readset(rs, keep_table=True)
+    rng = np.random.default_rng(9)
+    present = want.keys[rng.integers(0, len(want), 3000)]
+    # reverse-complement half of them through the oracle's own string helpers
+    strs = oracle.unpack(present[:1500], 51)
+    comp = str.maketrans("ACGT", "TGCA")
+    rc = oracle.pack([s.translate(comp)[::-1] for s in strs])
+    rand = oracle.pack(["".join("ACGT"[x] for x in rng.integers(0, 4, 51)) for _ in range(1000)])
+    # low-count keys (below min_depth) must answer as absent
+    low = oracle.run_readset(rs, min_depth=1)
+    singles = low.keys[low.counts == 1][:500]
+    q = np.concatenate([present, rc, rand, singles])
+    p = rs.meta["params"]
+    with KmerAnalysis(make_params(k=51, max_bases=rs.n_bases, max_reads=rs.n_reads,
+                                  expected_distinct=rs.n_bases, min_depth=p["min_depth"])) as ka:
+        seq, qual, offs = to_dev(gpu, rs)
+        ka.count(seq, qual, offs)
+        ka.finalize()
+        c, e, cd = ka.query(q)
+        qd = gpu.from_numpy(q.astype(np.int64)).cuda()
+        c2, e2, cd2 = ka.query(qd)
+        gpu.cuda.synchronize()
+    wc, we, wcd = want.query(q)
+    np.testing.assert_array_equal(c, wc)
+    np.testing.assert_array_equal(e, we)
+    np.testing.assert_array_equal(cd, wcd)
+    np.testing.assert_array_equal(c2.cpu().numpy().astype(np.uint32), wc)
+    np.testing.assert_array_equal(e2.cpu().numpy().astype(np.uint32), we)
+    assert (c[:3000] > 0).all() and (c[len(present) + 1500 + 1000:] == 0).all()
+
+
+def test_count_batch_equals_solo_and_oracle(gpu):
+    from paper_1705_11147_gb300 import KmerAnalysis, count_batch, finalize_batch, make_params
+    specs = synth.batched_specs(6, scale=0.02)
+    sets = [synth.sample_reads(s) for s in specs]
+    handles, reads = [], []
+    for rs in sets:
+        p = rs.meta["params"]
+        handles.append(KmerAnalysis(make_params(k=p["k"], min_depth=p["min_depth"], max_bases=rs.n_bases,
+                                                max_reads=rs.n_reads, expected_distinct=rs.n_bases)))
+        reads.append(to_dev(gpu, rs))
+    count_batch(handles, reads)
+    finalize_batch(handles)
+    for i, (h, rs) in enumerate(zip(handles, sets)):
+        got = h.copy_result().sorted()
+        assert_same(got, oracle.run_readset(rs), f"sample {i}")
+        assert_same(got, run_gpu(gpu, rs), f"sample {i} solo")
+        h.destroy()
+
+
+# ------------------------------------------------------------------ full-size sampled parity
+
+@pytest.mark.slow
+def test_large_200m_sampled_partition(gpu):
+    """6 Gbases, 4.8 G windows: the whole GPU result is checked on the k-mers of one owner
+    partition (1/256 of the key space, by the oracle's own hash), computed by the oracle
+    one partition at a time, plus the total window count."""
+    import bench
+    rs = synth.workload("large_200m")
+    got = bench.run_large_once(rs)
+    part, n_parts = 0, 256
+    sel = oracle.partition_of(got.keys, 51, n_parts) == part
+    sub = type(got)(got.keys[sel], got.counts[sel], got.ext[sel], got.codes[sel])
+    want = oracle.run_readset(rs, part=part, n_parts=n_parts)
+    assert_same(sub.sorted(), want, "large_200m partition 0/256")
+    assert got.valid_windows == want.valid_windows
