@@ -38,11 +38,12 @@ def run_gpu(torch, rs, device_inputs=True, batches=1, **kw):
     p.setdefault("expected_distinct", max(rs.n_bases, 1))
     with KmerAnalysis(make_params(**p)) as ka:
         cuts = np.linspace(0, rs.n_reads, batches + 1).astype(np.int64)
+        if device_inputs:
+            seq, qual, _ = to_dev(torch, rs)
         for b in range(batches):
             r0, r1 = int(cuts[b]), int(cuts[b + 1])
             offs = rs.offsets[r0:r1 + 1]
             if device_inputs:
-                seq, qual, o = to_dev(torch, rs)
                 ka.count(seq, qual, torch.from_numpy(offs.astype(np.int64)).cuda())
             else:
                 ka.count(rs.seq, rs.qual, offs)
@@ -59,14 +60,16 @@ def assert_same(got, want, what=""):
             raise AssertionError(f"{what}: field {f} differs at rows {bad}: {a[bad]} vs {b[bad]}")
 
 
+GPU_ONLY = ("use_bloom", "load_factor", "table_capacity", "block_threads", "windows_per_thread",
+            "warp_aggregate", "ctas_per_sm", "expected_distinct", "expected_keys", "staging_bytes",
+            "max_bases", "max_reads", "bloom_fpr")
+
+
 def oracle_for(rs, **kw):
     p = dict(rs.meta.get("params", {}))
-    p.pop("bloom_fpr", None)
-    for key in ("use_bloom", "load_factor", "table_capacity", "block_threads", "windows_per_thread",
-                "warp_aggregate", "ctas_per_sm", "expected_distinct", "expected_keys", "staging_bytes",
-                "max_bases", "max_reads", "bloom_fpr"):
-        kw.pop(key, None)
     p.update(kw)
+    for key in GPU_ONLY:
+        p.pop(key, None)
     return oracle.run(rs.seq, rs.qual, rs.offsets, **p)
 
 
@@ -179,7 +182,7 @@ def test_multiple_count_calls(gpu, plain):
     dict(block_threads=256, windows_per_thread=8, warp_aggregate=True),
     dict(block_threads=1024, windows_per_thread=2, ctas_per_sm=1),
     dict(block_threads=512, windows_per_thread=16, load_factor=0.85),
-    dict(expected_distinct=50_000, bloom_fpr=0.3),       # tiny, saturated Bloom filter
+    dict(expected_distinct=50_000, bloom_fpr=0.3, table_capacity=4_000_000),  # tiny, saturated Bloom
     dict(expected_distinct=200_000_000, bloom_fpr=0.001),  # huge filter
 ])
 def test_results_independent_of_tuning(gpu, plain, shape):
