@@ -251,7 +251,7 @@ def run_ours(args, ws, rank, local):
     qual = torch.from_numpy(rs.qual).to(dev)
     offs = torch.from_numpy(rs.offsets.astype(np.int64)).to(dev)
     stream = torch.cuda.current_stream(dev)
-    prm = make_handle_params(rs, n_parts=ws, part=rank)
+    prm = make_handle_params(rs, n_parts=ws, part=rank, **args.tuning)
     ka = KmerAnalysis(prm, stream=stream)
 
     # query set: 1 M k-mers present in the result + 1 M random k-mers (mostly absent)
@@ -336,6 +336,8 @@ def run_ours(args, ws, rank, local):
                       "parallelism": f"owner-computes x{ws}" if ws > 1 else "1 GPU",
                       "l2": "inputs (12 GB of reads, 33 GB table) far larger than L2; no flush"},
            "roofline": roof, "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
+           "tuning": {k2: getattr(prm, k2) for k2 in ("block_threads", "windows_per_thread", "ctas_per_sm",
+                                                      "warp_aggregate", "slot_prefetch")},
            "clocks": clk, "generation_s": round(t_gen, 1)}
     if e2e:
         out["e2e"] = e2e
@@ -450,7 +452,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--tune", action="append", default=[],
+                    help="launch-shape override key=value (block_threads, windows_per_thread, "
+                         "ctas_per_sm, warp_aggregate, slot_prefetch, load_factor)")
     args = ap.parse_args()
+    args.tuning = {}
+    for kv in args.tune:
+        key, val = kv.split("=", 1)
+        args.tuning[key] = float(val) if key == "load_factor" else int(val)
     ws, rank, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, ws, rank)

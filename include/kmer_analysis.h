@@ -43,7 +43,8 @@ extern "C" {
 #define KMA_EFULL (-3)     /* hash table or packed-read arena capacity exceeded: no partial result;
                               recreate with a larger table_capacity / max_bases and count again */
 #define KMA_ESTATE (-4)    /* call not allowed in the handle's state (count after finalize, ...) */
-#define KMA_ETIMEOUT (-5)  /* reserved: the kernels contain no device-side waits */
+#define KMA_ETIMEOUT (-5)  /* a bounded device-side wait (completion of the staging copies of
+                              the read-packing kernel) gave up: no partial result */
 #define KMA_EOVERFLOW (-6) /* a 32-bit k-mer counter would have wrapped */
 #define KMA_ECUDA (-7)     /* a CUDA runtime call failed (cudaGetLastError text via strerror) */
 
@@ -76,8 +77,8 @@ typedef struct {
   double load_factor;         /* target table load when table_capacity = 0 (0: 0.5) */
   uint64_t staging_bytes;     /* device staging buffer for host inputs (0: 256 MiB) */
   /* Launch shape (0 = library default; chosen by the autotuner per GPU and size class). */
-  uint32_t block_threads;     /* threads per CTA of the counting kernels: 128..1024, x32 */
-  uint32_t windows_per_thread;/* window starts one thread handles per tile: 1..16 */
+  uint32_t block_threads;     /* threads per CTA of the counting kernels: 64..256, x32 */
+  uint32_t windows_per_thread;/* window starts one thread handles per tile: 1, 2, 4 or 8 */
   uint32_t ctas_per_sm;       /* persistent grid = SMs x ctas_per_sm (0: occupancy bound) */
   uint32_t warp_aggregate;    /* 1: merge identical keys inside a warp before the atomics */
   /* Owner-computes partition (Section 5.1: a deterministic k-mer -> owner map makes every
@@ -86,6 +87,11 @@ typedef struct {
    * The owner of a k-mer is a hash of its canonical key (library-defined, fixed). */
   uint32_t n_parts;           /* 0 or 1: no partition */
   uint32_t part;              /* 0 .. n_parts-1 */
+  uint32_t slot_prefetch;     /* Bloom pass: prefetch each window's table slot into L2 while
+                                 its Bloom word is tested. 0: default (off), 1: on, 2: off */
+  uint32_t fault_inject;      /* testing only. 0: off. 1: the read-packing kernel waits for
+                                 staging copies it never issued, with a short poll limit, so
+                                 its bounded wait gives up and the handle reports KMA_ETIMEOUT */
 } kma_params;
 
 /* Sizes derived from a kma_params (pure host arithmetic, no GPU needed). */

@@ -3,11 +3,11 @@
 The work runs in libkmer_analysis.so (CUDA, sm_103a), reached through the C ABI declared in
 include/kmer_analysis.h. This package is the thin Python binding over it.
 """
-from .capi import (KMA_CODE_F, KMA_CODE_X, KMA_EFULL, KMA_EINVAL, KMA_ESTATE, KMA_OK, KmaError,
-                   load)
+from .capi import (KMA_CODE_F, KMA_CODE_X, KMA_EFULL, KMA_EINVAL, KMA_ESTATE, KMA_ETIMEOUT, KMA_OK,
+                   KmaError, load)
 from .kmer_analysis import (KmerAnalysis, Result, count_batch, count_kmers, finalize_batch,
                             make_params, plan)
 
 __all__ = ["KmerAnalysis", "Result", "count_batch", "count_kmers", "finalize_batch",
            "make_params", "plan", "load", "KmaError", "KMA_OK", "KMA_EINVAL", "KMA_EFULL",
-           "KMA_ESTATE", "KMA_CODE_X", "KMA_CODE_F"]
+           "KMA_ESTATE", "KMA_ETIMEOUT", "KMA_CODE_X", "KMA_CODE_F"]

@@ -33,7 +33,8 @@ class kma_params(ctypes.Structure):
                 ("bloom_fpr", dbl), ("table_capacity", u64), ("expected_keys", u64),
                 ("load_factor", dbl), ("staging_bytes", u64),
                 ("block_threads", u32), ("windows_per_thread", u32), ("ctas_per_sm", u32),
-                ("warp_aggregate", u32), ("n_parts", u32), ("part", u32)]
+                ("warp_aggregate", u32), ("n_parts", u32), ("part", u32),
+                ("slot_prefetch", u32), ("fault_inject", u32)]
 
 
 class kma_plan(ctypes.Structure):

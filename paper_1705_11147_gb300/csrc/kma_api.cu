@@ -102,9 +102,13 @@ int check_params(const kma_params* p) {
   if (p->bloom_fpr < 0 || p->bloom_fpr >= 1) return KMA_EINVAL;
   if (p->load_factor < 0 || p->load_factor > 0.95) return KMA_EINVAL;
   if (p->max_bases == 0) return KMA_EINVAL;
-  if (p->block_threads && (p->block_threads < 128 || p->block_threads > 1024 || p->block_threads % 32))
+  if (p->block_threads && (p->block_threads < 64 || p->block_threads > 256 || p->block_threads % 32))
     return KMA_EINVAL;
-  if (p->windows_per_thread > 16) return KMA_EINVAL;
+  if (p->windows_per_thread && p->windows_per_thread != 1 && p->windows_per_thread != 2 &&
+      p->windows_per_thread != 4 && p->windows_per_thread != 8)
+    return KMA_EINVAL;
+  if (p->slot_prefetch > 2) return KMA_EINVAL;
+  if (p->fault_inject > 1) return KMA_EINVAL;
   if (p->n_parts > 1 && p->part >= p->n_parts) return KMA_EINVAL;
   return KMA_OK;
 }
@@ -178,6 +182,7 @@ struct kma_handle {
   cudaMemPool_t pool = nullptr;
   LaunchShape shape{256, 4, 0};
   bool agg = false;
+  unsigned prefetch = 1;
 
   u64* codes = nullptr;
   u64* inv = nullptr;
@@ -307,8 +312,9 @@ int clear_state(kma_handle* h) {
 
 void choose_shape(kma_handle* h) {
   h->shape.block_threads = h->p.block_threads ? (int)h->p.block_threads : 256;
-  h->shape.windows_per_thread = h->p.windows_per_thread ? (int)h->p.windows_per_thread : 4;
+  h->shape.windows_per_thread = h->p.windows_per_thread ? (int)h->p.windows_per_thread : 2;
   h->agg = h->p.warp_aggregate != 0;
+  h->prefetch = h->p.slot_prefetch == 1 ? 1u : 0u;
   int per_sm = h->p.ctas_per_sm ? (int)h->p.ctas_per_sm
                                 : pass_max_ctas_per_sm(h->shape.block_threads, h->shape.windows_per_thread, h->agg);
   if (per_sm < 1) per_sm = 1;
@@ -316,6 +322,7 @@ void choose_shape(kma_handle* h) {
 }
 
 int flags_to_code(unsigned flags) {
+  if (flags & kFlagTimeout) return KMA_ETIMEOUT;
   if (flags & kFlagBadOffsets) return KMA_EINVAL;
   if (flags & kFlagFull) return KMA_EFULL;
   if (flags & kFlagOverflow) return KMA_EOVERFLOW;
@@ -342,6 +349,13 @@ PassDesc pass_desc(kma_handle* h, unsigned mode, u64 q0, u64 q1) {
   return d;
 }
 
+// Staging-copy wait policy of the pack kernel: a generous poll limit, or (fault injection
+// for tests) copies that are never issued and a short limit, which must end in KMA_ETIMEOUT.
+void set_pack_waits(kma_handle* h, PackBatch& pb) {
+  pb.skip_copy = h->p.fault_inject == 1 ? 1u : 0u;
+  pb.wait_limit = h->p.fault_inject == 1 ? (1u << 10) : (1u << 22);
+}
+
 // Reserve arena space for a batch and describe it for the pack kernel.
 int reserve_batch(kma_handle* h, u64 n_reads, u64 n_bases, PackDesc& pd, u64& q0, u64& n_pos) {
   n_pos = ((n_bases + n_reads + 63) / 64) * 64;
@@ -363,15 +377,17 @@ int run_pack_and_pass(kma_handle* h, const PackDesc& pd) {
   PackBatch pb;
   std::memset(&pb, 0, offsetof(PackBatch, d) + sizeof(PackDesc));
   pb.n = 1;
+  set_pack_waits(h, pb);
   pb.d[0] = pd;
-  pb.d[0].word_begin = 0;
-  pb.total_words = pd.n_pos / 64;
-  int rc = timed_launch(h, KMA_KERNEL_PACK, h->stream, pb.total_words > 0,
+  pb.d[0].chunk_begin = 0;
+  pb.total_chunks = (pd.n_pos / 64 + kPackChunkWords - 1) / kPackChunkWords;
+  int rc = timed_launch(h, KMA_KERNEL_PACK, h->stream, pb.total_chunks > 0,
                         [&] { return launch_pack(pb, h->stream, h->num_sms); });
   if (rc) return rc;
   PassBatch b;
   std::memset(&b, 0, offsetof(PassBatch, d) + sizeof(PassDesc));
   b.n = 1;
+  b.prefetch = h->prefetch;
   b.d[0] = pass_desc(h, h->p.use_bloom ? kModeBloom : kModeCount, pd.q0, pd.q0 + pd.n_pos);
   const u64 tile = (u64)h->shape.block_threads * h->shape.windows_per_thread;
   b.d[0].tile_begin = 0;
@@ -534,8 +550,9 @@ int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual, const 
     PackBatch pb;
     std::memset(&pb, 0, offsetof(PackBatch, d) + sizeof(PackDesc));
     pb.n = 1;
+    set_pack_waits(h, pb);
     pb.d[0] = pd;
-    pb.total_words = n_pos / 64;
+    pb.total_chunks = (n_pos / 64 + kPackChunkWords - 1) / kPackChunkWords;
     if ((rc = timed_launch(h, KMA_KERNEL_PACK, h->stream, true,
                            [&] { return launch_pack(pb, h->stream, h->num_sms); })))
       return rc;
@@ -543,6 +560,7 @@ int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual, const 
     PassBatch pb2;
     std::memset(&pb2, 0, offsetof(PassBatch, d) + sizeof(PassDesc));
     pb2.n = 1;
+    pb2.prefetch = h->prefetch;
     pb2.d[0] = pass_desc(h, h->p.use_bloom ? kModeBloom : kModeCount, q0, q0 + n_pos);
     const u64 tile = (u64)h->shape.block_threads * h->shape.windows_per_thread;
     pb2.total_tiles = (n_pos + tile - 1) / tile;
@@ -578,6 +596,7 @@ static int finalize_many(kma_handle* const* hs, uint32_t n, kma_result* out) {
   // 1. recount pass over the Bloom handles
   PassBatch pb;
   std::memset(&pb, 0, sizeof(pb));
+  pb.prefetch = h0->prefetch;
   const u64 tile = (u64)h0->shape.block_threads * h0->shape.windows_per_thread;
   u64 tiles = 0;
   for (uint32_t i = 0; i < n; ++i) {
@@ -670,8 +689,10 @@ int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uin
   }
   PackBatch pk;
   std::memset(&pk, 0, sizeof(pk));
+  set_pack_waits(h0, pk);
   PassBatch ps;
   std::memset(&ps, 0, sizeof(ps));
+  ps.prefetch = h0->prefetch;
   const u64 tile = (u64)h0->shape.block_threads * h0->shape.windows_per_thread;
   u64 words = 0, tiles = 0;
   for (uint32_t i = 0; i < n; ++i) {
@@ -685,15 +706,15 @@ int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uin
     pd.qual = (const unsigned char*)reads[i].qual;
     pd.offsets = (const unsigned long long*)reads[i].offsets;
     pd.delta = 0;
-    pd.word_begin = words;
-    words += n_pos / 64;
+    pd.chunk_begin = words;
+    words += (n_pos / 64 + kPackChunkWords - 1) / kPackChunkWords;
     pk.d[pk.n++] = pd;
     PassDesc d = pass_desc(h, h->p.use_bloom ? kModeBloom : kModeCount, q0, q0 + n_pos);
     d.tile_begin = tiles;
     tiles += (n_pos + tile - 1) / tile;
     ps.d[ps.n++] = d;
   }
-  pk.total_words = words;
+  pk.total_chunks = words;
   ps.total_tiles = tiles;
   int rc = timed_launch(h0, KMA_KERNEL_PACK, h0->stream, pk.n > 0 && words > 0,
                         [&] { return launch_pack(pk, h0->stream, h0->num_sms); });

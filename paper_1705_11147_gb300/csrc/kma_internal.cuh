@@ -26,6 +26,7 @@ constexpr int kMaxBatch = 64;
 constexpr uint32_t kFlagFull = 1u;
 constexpr uint32_t kFlagOverflow = 2u;
 constexpr uint32_t kFlagBadOffsets = 4u;
+constexpr uint32_t kFlagTimeout = 8u;     // a bounded device wait gave up
 
 // One hash-table slot: the key and count share the first 32-byte sector, the eight
 // extension counters fill the second, so an update touches one half cache line.
@@ -72,7 +73,7 @@ struct PassDesc {
 
 struct PassBatch {
   unsigned int n;
-  unsigned int pad;
+  unsigned int prefetch;          // 1: L2-prefetch each window's first table slot in the Bloom pass
   unsigned long long total_tiles;
   PassDesc d[kMaxBatch];
 };
@@ -91,7 +92,7 @@ struct PackDesc {
   unsigned long long n_bases;         // offsets[n_reads] - offsets[0] as the host believes
   unsigned long long q0;              // arena start (multiple of 64)
   unsigned long long n_pos;           // n_bases + n_reads, rounded up to a multiple of 64
-  unsigned long long word_begin;      // prefix of 64-position words over the batch
+  unsigned long long chunk_begin;     // prefix of 256-word pack chunks over the batch
   unsigned long long* codes;
   unsigned long long* inv;
   unsigned long long* hq;
@@ -100,10 +101,14 @@ struct PackDesc {
   unsigned int pad;
 };
 
+constexpr unsigned long long kPackChunkWords = 256;  // 64-position words per pack CTA chunk
+
 struct PackBatch {
   unsigned int n;
+  unsigned int skip_copy;             // testing: wait for staging copies that were never issued
+  unsigned int wait_limit;            // polls of the staging barrier before giving up
   unsigned int pad;
-  unsigned long long total_words;
+  unsigned long long total_chunks;
   PackDesc d[kMaxBatch];
 };
 

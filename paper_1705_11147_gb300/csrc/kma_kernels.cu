@@ -230,10 +230,55 @@ __device__ __forceinline__ int find_pass_sample(const PassBatch& B, u64 t) {
   return lo;
 }
 
-template <bool AGG>
-__global__ void __launch_bounds__(1024) pass_kernel(const __grid_constant__ PassBatch B, int wpt) {
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Insert-if-absent continuing from a first probe whose slot (index idx) is already loaded.
+__device__ __forceinline__ Slot* resolve_insert(Slot* table, u64 slots, u64 idx, ulonglong2 kv,
+                                                u64 lo, u64 hi, bool& inserted) {
+  const u64 limit = slots < kMaxProbe ? slots : kMaxProbe;
+  inserted = false;
+  for (u64 n = 0; n < limit; ++n) {
+    Slot* s = table + idx;
+    if (n) kv = __ldcg(reinterpret_cast<const ulonglong2*>(s));
+    if (kv.x == lo && kv.y == hi) return s;
+    if (kv.y == kEmpty || kv.x == kEmpty) {
+      u64 olo, ohi;
+      cas128(s, kEmpty, kEmpty, lo, hi, olo, ohi);
+      if (olo == kEmpty && ohi == kEmpty) { inserted = true; return s; }
+      if (olo == lo && ohi == hi) return s;
+    }
+    idx = (idx + 1 == slots) ? 0 : idx + 1;
+  }
+  return nullptr;
+}
+
+// Lookup (table not being modified) continuing from a loaded first probe.
+__device__ __forceinline__ Slot* resolve_find(Slot* table, u64 slots, u64 idx, ulonglong2 kv,
+                                              u64 lo, u64 hi, bool& full) {
+  const u64 limit = slots < kMaxProbe ? slots : kMaxProbe;
+  full = false;
+  for (u64 n = 0; n < limit; ++n) {
+    Slot* s = table + idx;
+    if (n) kv = __ldcg(reinterpret_cast<const ulonglong2*>(s));
+    if (kv.x == lo && kv.y == hi) return s;
+    if (kv.y == kEmpty) return nullptr;
+    idx = (idx + 1 == slots) ? 0 : idx + 1;
+  }
+  full = true;
+  return nullptr;
+}
+
+// One tile = blockDim.x * WPT consecutive window starts; thread t takes starts
+// base + j * blockDim.x + t (j < WPT), so a warp always covers 32 consecutive, 32-aligned
+// starts (one marks word). The WPT windows of a thread go through the memory stages
+// together: all Bloom atomics (with an L2 prefetch of each window's first table slot) are in
+// flight at once, then all first probes, then the updates.
+template <int WPT, bool AGG>
+__global__ void __launch_bounds__(256) pass_kernel(const __grid_constant__ PassBatch B) {
   const unsigned lane = threadIdx.x & 31;
-  const u64 tile = (u64)blockDim.x * (u64)wpt;
+  const u64 tile = (u64)blockDim.x * WPT;
   // Per-warp running totals, flushed when the warp moves to another sample.
   int cur = -1;
   u64 acc_valid = 0, acc_ins = 0, acc_first = 0;
@@ -250,55 +295,94 @@ __global__ void __launch_bounds__(1024) pass_kernel(const __grid_constant__ Pass
       cur = si;
       acc_valid = acc_ins = acc_first = 0;
     }
-    const u64 base = D.q0 + (t - D.tile_begin) * tile;
-    for (int j = 0; j < wpt; ++j) {
-      const u64 q = base + (u64)j * blockDim.x + threadIdx.x;
-      if (q - lane >= D.q1) break;  // whole warp past the end (q1 is a multiple of 64)
-      Window w;
-      if (D.mode == kModeRecount) {
-        const unsigned mw = D.marks[q >> 5];
-        if (!((mw >> lane) & 1u)) continue;
-        if (!load_window(D, q, w)) continue;  // cannot happen: marks are set on valid windows
-        const u64 h = key_hash(w.lo, w.hi);
-        bool full;
-        Slot* s = const_cast<Slot*>(find(D.table, D.slots, w.lo, w.hi, h, full));
-        if (full) atomicOr(&D.status->flags, kFlagFull);
-        if (s) add_occurrence(s, w, 1u, D.status);
-        continue;
-      }
-      bool valid = q < D.q1 && load_window(D, q, w);
-      u64 h = 0;
-      if (valid) {
-        h = key_hash(w.lo, w.hi);
-        if (D.n_parts > 1 && owner_of(h, D.n_parts) != D.part) valid = false;  // not ours
-      }
-      bool count_it = valid;
-      if (D.mode == kModeBloom) {
-        bool first = false;
-        if (valid) {
-          const u64 m = bloom_mask(h, D.bloom_h);
-          const u64 old = atomicOr(D.bloom + bloom_index(h, D.bloom_words), m);
-          first = (old & m) != m;
+    const u64 base = D.q0 + (t - D.tile_begin) * tile + threadIdx.x;
+    const unsigned mode = D.mode;
+    Window w[WPT];
+    u64 h[WPT];
+    bool in[WPT], act[WPT];
+
+    // stage 1: extract the windows (packed reads are read coalesced through L1)
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) {
+      const u64 q = base + (u64)j * blockDim.x;
+      in[j] = (q - lane) < D.q1;  // warp-uniform: q1 is a multiple of 64
+      act[j] = false;
+      h[j] = 0;
+      if (in[j]) {
+        bool ok = (mode != kModeRecount) || ((D.marks[q >> 5] >> lane) & 1u);
+        ok = ok && load_window(D, q, w[j]);
+        if (ok) {
+          h[j] = key_hash(w[j].lo, w[j].hi);
+          if (D.n_parts > 1 && owner_of(h[j], D.n_parts) != D.part) ok = false;  // not ours
         }
-        const unsigned mark = __ballot_sync(0xffffffffu, first);
-        if (lane == 0) D.marks[q >> 5] = mark;
-        acc_first += __popc(mark);
-        count_it = valid && !first;
+        act[j] = ok;
       }
-      const unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
-      acc_valid += nv;
+    }
+
+    // stage 2: Bloom test-and-set of every window, first sightings marked
+    if (mode == kModeBloom) {
+      u64 old[WPT], msk[WPT];
+#pragma unroll
+      for (int j = 0; j < WPT; ++j) {
+        old[j] = 0;
+        msk[j] = 0;
+        if (act[j]) {
+          msk[j] = bloom_mask(h[j], D.bloom_h);
+          if (B.prefetch) prefetch_l2(D.table + table_index(h[j], D.slots));
+          old[j] = atomicOr(D.bloom + bloom_index(h[j], D.bloom_words), msk[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < WPT; ++j) {
+        if (!in[j]) continue;
+        const bool first = act[j] && (old[j] & msk[j]) != msk[j];
+        const unsigned mark = __ballot_sync(0xffffffffu, first);
+        if (lane == 0) D.marks[(base + (u64)j * blockDim.x) >> 5] = mark;
+        acc_first += __popc(mark);
+        acc_valid += __popc(__ballot_sync(0xffffffffu, act[j]));
+        act[j] = act[j] && !first;
+      }
+    } else if (mode == kModeCount) {
+#pragma unroll
+      for (int j = 0; j < WPT; ++j)
+        if (in[j]) acc_valid += __popc(__ballot_sync(0xffffffffu, act[j]));
+    }
+
+    // stage 3: first probe of every window that counts
+    ulonglong2 kv[WPT];
+    u64 idx[WPT];
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) {
+      kv[j] = make_ulonglong2(0, 0);
+      idx[j] = 0;
+      if (act[j]) {
+        idx[j] = table_index(h[j], D.slots);
+        kv[j] = __ldcg(reinterpret_cast<const ulonglong2*>(D.table + idx[j]));
+      }
+    }
+
+    // stage 4: finish the probe (insert-if-absent, or find in the recount) and count
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) {
       Slot* s = nullptr;
       bool inserted = false;
-      if (count_it) {
-        s = find_or_insert(D.table, D.slots, w.lo, w.hi, h, inserted);
-        if (!s) atomicOr(&D.status->flags, kFlagFull);
+      if (act[j]) {
+        if (mode == kModeRecount) {
+          bool full;
+          s = resolve_find(D.table, D.slots, idx[j], kv[j], w[j].lo, w[j].hi, full);
+          if (full) atomicOr(&D.status->flags, kFlagFull);
+        } else {
+          s = resolve_insert(D.table, D.slots, idx[j], kv[j], w[j].lo, w[j].hi, inserted);
+          if (!s) atomicOr(&D.status->flags, kFlagFull);
+        }
       }
+      if (!in[j]) continue;
       acc_ins += __popc(__ballot_sync(0xffffffffu, inserted));
       if (AGG) {
-        const unsigned act = __ballot_sync(0xffffffffu, s != nullptr);
-        if (s) add_occurrence_agg(act, s, w, D.status);
-      } else {
-        if (s) add_occurrence(s, w, 1u, D.status);
+        const unsigned a = __ballot_sync(0xffffffffu, s != nullptr);
+        if (s) add_occurrence_agg(a, s, w[j], D.status);
+      } else if (s) {
+        add_occurrence(s, w[j], 1u, D.status);
       }
     }
   }
@@ -311,70 +395,189 @@ __global__ void __launch_bounds__(1024) pass_kernel(const __grid_constant__ Pass
 
 // ------------------------------------------------------------------ pack kernel
 
-__device__ __forceinline__ int find_pack_sample(const PackBatch& B, u64 w) {
+__device__ __forceinline__ int find_pack_sample(const PackBatch& B, u64 c) {
   int lo = 0, hi = (int)B.n;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (B.d[mid].word_begin <= w) lo = mid; else hi = mid;
+    if (B.d[mid].chunk_begin <= c) lo = mid; else hi = mid;
   }
   return lo;
 }
 
-// One thread per 64 arena positions: writes two code words, one invalid word, one hq word.
-__global__ void __launch_bounds__(256) pack_kernel(const __grid_constant__ PackBatch B) {
-  const u64 stride = (u64)gridDim.x * blockDim.x;
-  for (u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x; w < B.total_words; w += stride) {
-    const int si = find_pack_sample(B, w);
+// Last read r with start ps_r = offsets[r] - o0 + r <= p (reads of the batch: [lo, n)).
+__device__ __forceinline__ u64 read_at(const u64* off, u64 o0, u64 n, u64 lo, u64 p) {
+  u64 hi = n;
+  while (hi - lo > 1) {
+    const u64 mid = (lo + hi) >> 1;
+    if (off[mid] - o0 + mid <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Batch-relative index of the first base at or after arena position p (clamped to n_bases).
+__device__ __forceinline__ u64 base_at_or_after(const PackDesc& D, u64 o0, u64 p) {
+  if (D.n_reads == 0) return 0;
+  const u64* off = D.offsets;
+  const u64 r = read_at(off, o0, D.n_reads, 0, p);
+  const u64 rs = off[r] - o0 + r;
+  const u64 len = off[r + 1] - off[r];
+  u64 b = (p - rs < len) ? off[r] - o0 + (p - rs) : off[r + 1] - o0;
+  return b < D.n_bases ? b : D.n_bases;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// 1-D TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
+// completion signalled on the mbarrier as transaction bytes.
+__device__ __forceinline__ void tma_load_1d(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned phase) {
+  unsigned done;
+  asm volatile("{\n\t.reg .pred p;\n\t"
+               "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(done) : "r"(bar), "r"(phase) : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the mbarrier phase: returns false (and the caller raises a status flag)
+// if the copies have not completed after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned phase, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+constexpr int kPackThreads = 256;                     // one thread per 64 positions
+constexpr int kPackChunk = kPackThreads * 64;         // positions per CTA chunk
+constexpr int kPackBuf = kPackChunk + 32;             // staged bytes (+ alignment slack)
+
+// One CTA chunk = 256 words of 64 arena positions of one sample. The bases (and qualities)
+// the chunk covers are one contiguous byte range of the input; thread 0 locates it and
+// stages it into shared memory with two 1-D TMA bulk copies; then every thread packs its 64
+// positions from shared memory into two code words, one invalid word and one hq word.
+__global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constant__ PackBatch B) {
+  __shared__ __align__(16) unsigned char s_seq[kPackBuf];
+  __shared__ __align__(16) unsigned char s_qual[kPackBuf];
+  __shared__ __align__(8) unsigned long long s_bar;
+  __shared__ u64 s_b0, s_b1, s_r0;
+  __shared__ unsigned s_lead, s_ok;
+  const unsigned bar = smem_u32(&s_bar);
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  unsigned phase = 0;
+
+  for (u64 c = blockIdx.x; c < B.total_chunks; c += gridDim.x) {
+    const int si = find_pack_sample(B, c);
     const PackDesc& D = B.d[si];
-    const u64 lw = w - D.word_begin;
-    const u64 p0 = lw * 64;  // batch-relative position
     const u64* off = D.offsets;
     const u64 o0 = off[0];
-    if (lw == 0 && off[D.n_reads] - o0 != D.n_bases) atomicOr(&D.status->flags, kFlagBadOffsets);
-    // Read r starts at ps_r = offsets[r] - o0 + r; find the last read starting at or before p0.
-    u64 r = 0;
-    if (D.n_reads > 0) {
-      u64 lo = 0, hi = D.n_reads;
-      while (hi - lo > 1) {
-        const u64 mid = (lo + hi) >> 1;
-        if (off[mid] - o0 + mid <= p0) lo = mid; else hi = mid;
+    const u64 words = D.n_pos / 64;
+    const u64 w0 = (c - D.chunk_begin) * kPackThreads;
+    const u64 w1 = (w0 + kPackThreads < words) ? w0 + kPackThreads : words;
+    if (threadIdx.x == 0) {
+      if (w0 == 0 && off[D.n_reads] - o0 != D.n_bases) atomicOr(&D.status->flags, kFlagBadOffsets);
+      u64 b0 = base_at_or_after(D, o0, w0 * 64);
+      u64 b1 = base_at_or_after(D, o0, w1 * 64);
+      unsigned ok = 1;
+      if (b1 < b0 || b1 - b0 > (u64)kPackChunk) {  // only possible with inconsistent offsets
+        atomicOr(&D.status->flags, kFlagBadOffsets);
+        b1 = b0;
+        ok = 0;
       }
-      r = lo;
-    }
-    u64 rs = D.n_reads ? off[r] - o0 + r : 0;        // start of read r
-    u64 re = D.n_reads ? off[r + 1] - o0 + r : 0;    // its separator position
-    if (D.n_reads && off[r + 1] < off[r]) atomicOr(&D.status->flags, kFlagBadOffsets);
-    u64 c0 = 0, c1 = 0, inv = 0, hq = 0;
-    for (int i = 0; i < 64; ++i) {
-      const u64 p = p0 + i;
-      while (r < D.n_reads && p > re) {  // move to the read containing p
-        ++r;
-        if (r < D.n_reads) {
-          rs = off[r] - o0 + r;
-          re = off[r + 1] - o0 + r;
-          if (off[r + 1] < off[r]) atomicOr(&D.status->flags, kFlagBadOffsets);
+      const u64 a = reinterpret_cast<u64>(D.seq) + o0 + b0 - (u64)D.delta;
+      const u64 aq = reinterpret_cast<u64>(D.qual) + o0 + b0 - (u64)D.delta;
+      const unsigned lead = (unsigned)(a & 15);
+      // the quality array must share the alignment phase to reuse `lead`; otherwise
+      // stage it from its own aligned base (lead differs) -- handled by two leads below
+      const unsigned leadq = (unsigned)(aq & 15);
+      const unsigned n = (unsigned)(b1 - b0);
+      s_b0 = b0;
+      s_b1 = b1;
+      s_r0 = D.n_reads ? read_at(off, o0, D.n_reads, 0, w0 * 64) : 0;
+      s_lead = lead | (leadq << 8);
+      s_ok = ok;
+      if (n) {
+        const unsigned bytes = (lead + n + 15u) & ~15u;
+        const unsigned bytesq = (leadq + n + 15u) & ~15u;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, bytes + bytesq);
+        if (!B.skip_copy) {
+          tma_load_1d(smem_u32(s_seq), reinterpret_cast<const void*>(a - lead), bytes, bar);
+          tma_load_1d(smem_u32(s_qual), reinterpret_cast<const void*>(aq - leadq), bytesq, bar);
         }
       }
-      unsigned code = 0, valid = 0, good = 0;
-      // batch-relative base index; only bases inside [0, n_bases) are ever read
-      const u64 bidx = off[r] - o0 + (p - rs);
-      if (r < D.n_reads && p < re && p >= rs && bidx < D.n_bases) {
-        const u64 b = o0 + bidx - (u64)D.delta;
-        const unsigned ch = D.seq[b] & 0xDFu;
-        valid = (ch == 'A') | (ch == 'C') | (ch == 'G') | (ch == 'T');
-        code = ch == 'C' ? 1u : ch == 'G' ? 2u : ch == 'T' ? 3u : 0u;
-        good = valid && (unsigned)D.qual[b] >= D.qual_min;
-      }
-      if (i < 32) c0 |= (u64)code << (62 - 2 * i);
-      else c1 |= (u64)code << (62 - 2 * (i - 32));
-      inv |= (u64)(!valid) << (63 - i);
-      hq |= (u64)good << (63 - i);
     }
-    const u64 gw = (D.q0 >> 6) + lw;
-    D.codes[2 * gw] = c0;
-    D.codes[2 * gw + 1] = c1;
-    D.inv[gw] = inv;
-    D.hq[gw] = hq;
+    // thread 0 waits for the two copies (bounded); the block barrier then publishes the
+    // staged bytes to every thread
+    if (threadIdx.x == 0 && s_b1 > s_b0) {
+      if (mbar_wait_bounded(bar, phase, B.wait_limit)) {
+        phase ^= 1u;
+      } else {
+        atomicOr(&D.status->flags, kFlagTimeout);
+        if (!B.skip_copy) mbar_wait_bounded(bar, phase, B.wait_limit);  // copies may still land
+        s_ok = 2;
+      }
+    }
+    __syncthreads();
+    if (s_ok == 2) return;  // uniform: the chunk's input never arrived
+    const u64 b0 = s_b0, b1 = s_b1;
+    const unsigned lead = s_lead & 0xFF, leadq = s_lead >> 8;
+    const u64 w = w0 + threadIdx.x;
+    if (w < w1 && s_ok) {
+      const u64 p0 = w * 64;
+      u64 r = D.n_reads ? read_at(off, o0, D.n_reads, s_r0, p0) : 0;
+      u64 rs = D.n_reads ? off[r] - o0 + r : 0;
+      u64 re = D.n_reads ? off[r + 1] - o0 + r : 0;
+      u64 c0 = 0, c1 = 0, inv = 0, hq = 0;
+#pragma unroll 4
+      for (int i = 0; i < 64; ++i) {
+        const u64 p = p0 + i;
+        while (r < D.n_reads && p > re) {  // move to the read containing p
+          ++r;
+          if (r < D.n_reads) {
+            rs = off[r] - o0 + r;
+            re = off[r + 1] - o0 + r;
+          }
+        }
+        unsigned code = 0, valid = 0, good = 0;
+        const u64 bidx = off[r] - o0 + (p - rs);
+        if (r < D.n_reads && p < re && p >= rs && bidx >= b0 && bidx < b1) {
+          const unsigned ch = s_seq[lead + (unsigned)(bidx - b0)] & 0xDFu;
+          valid = (ch == 'A') | (ch == 'C') | (ch == 'G') | (ch == 'T');
+          code = ch == 'C' ? 1u : ch == 'G' ? 2u : ch == 'T' ? 3u : 0u;
+          good = valid && (unsigned)s_qual[leadq + (unsigned)(bidx - b0)] >= D.qual_min;
+        }
+        if (i < 32) c0 |= (u64)code << (62 - 2 * i);
+        else c1 |= (u64)code << (62 - 2 * (i - 32));
+        inv |= (u64)(!valid) << (63 - i);
+        hq |= (u64)good << (63 - i);
+      }
+      const u64 gw = (D.q0 >> 6) + w;
+      reinterpret_cast<ulonglong2*>(D.codes)[gw] = make_ulonglong2(c0, c1);
+      D.inv[gw] = inv;
+      D.hq[gw] = hq;
+    } else if (w < w1) {
+      const u64 gw = (D.q0 >> 6) + w;
+      reinterpret_cast<ulonglong2*>(D.codes)[gw] = make_ulonglong2(0, 0);
+      D.inv[gw] = ~0ull;
+      D.hq[gw] = 0;
+    }
+    __syncthreads();  // shared buffers are reused by the next chunk
   }
 }
 
@@ -540,29 +743,50 @@ __global__ void __launch_bounds__(256) table_init_kernel(Slot* table, u64 slots)
 
 // ------------------------------------------------------------------ launchers
 
-int pass_max_ctas_per_sm(int block_threads, int wpt, bool agg) {
-  (void)wpt;
+template <int WPT, bool AGG>
+static cudaError_t launch_pass_t(const PassBatch& b, int grid, int threads, cudaStream_t stream) {
+  pass_kernel<WPT, AGG><<<(unsigned)grid, threads, 0, stream>>>(b);
+  return cudaGetLastError();
+}
+
+template <int WPT, bool AGG>
+static int occupancy_t(int threads) {
   int n = 0;
-  cudaError_t e = agg ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pass_kernel<true>, block_threads, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pass_kernel<false>, block_threads, 0);
-  return e == cudaSuccess ? n : 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pass_kernel<WPT, AGG>, threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int pass_max_ctas_per_sm(int block_threads, int wpt, bool agg) {
+  switch (wpt) {
+    case 1: return agg ? occupancy_t<1, true>(block_threads) : occupancy_t<1, false>(block_threads);
+    case 2: return agg ? occupancy_t<2, true>(block_threads) : occupancy_t<2, false>(block_threads);
+    case 4: return agg ? occupancy_t<4, true>(block_threads) : occupancy_t<4, false>(block_threads);
+    default: return agg ? occupancy_t<8, true>(block_threads) : occupancy_t<8, false>(block_threads);
+  }
 }
 
 cudaError_t launch_pass(const PassBatch& b, const LaunchShape& shape, bool agg, cudaStream_t stream) {
   if (b.total_tiles == 0) return cudaSuccess;
   u64 grid = (u64)shape.grid;
   if (grid > b.total_tiles) grid = b.total_tiles;
-  if (agg) pass_kernel<true><<<(unsigned)grid, shape.block_threads, 0, stream>>>(b, shape.windows_per_thread);
-  else pass_kernel<false><<<(unsigned)grid, shape.block_threads, 0, stream>>>(b, shape.windows_per_thread);
-  return cudaGetLastError();
+  const int g = (int)grid, th = shape.block_threads;
+  switch (shape.windows_per_thread) {
+    case 1: return agg ? launch_pass_t<1, true>(b, g, th, stream) : launch_pass_t<1, false>(b, g, th, stream);
+    case 2: return agg ? launch_pass_t<2, true>(b, g, th, stream) : launch_pass_t<2, false>(b, g, th, stream);
+    case 4: return agg ? launch_pass_t<4, true>(b, g, th, stream) : launch_pass_t<4, false>(b, g, th, stream);
+    default: return agg ? launch_pass_t<8, true>(b, g, th, stream) : launch_pass_t<8, false>(b, g, th, stream);
+  }
 }
 
 cudaError_t launch_pack(const PackBatch& b, cudaStream_t stream, int num_sms) {
-  if (b.total_words == 0) return cudaSuccess;
-  u64 blocks = (b.total_words + 255) / 256;
-  const u64 cap = (u64)num_sms * 8;
+  if (b.total_chunks == 0) return cudaSuccess;
+  u64 blocks = b.total_chunks;
+  const u64 cap = (u64)num_sms * 4;
   if (blocks > cap) blocks = cap;
-  pack_kernel<<<(unsigned)blocks, 256, 0, stream>>>(b);
+  pack_kernel<<<(unsigned)blocks, kPackThreads, 0, stream>>>(b);
   return cudaGetLastError();
 }
 

@@ -67,6 +67,10 @@ def test_param_validation(lib):
     assert _plan_rc(k=31, max_bases=1000, min_depth=1, use_bloom=False) == 0
     assert _plan_rc(k=31, max_bases=0) == capi.KMA_EINVAL
     assert _plan_rc(k=31, max_bases=1000, block_threads=100) == capi.KMA_EINVAL
+    assert _plan_rc(k=31, max_bases=1000, block_threads=512) == capi.KMA_EINVAL
+    assert _plan_rc(k=31, max_bases=1000, windows_per_thread=3) == capi.KMA_EINVAL
+    assert _plan_rc(k=31, max_bases=1000, windows_per_thread=8) == 0
+    assert _plan_rc(k=31, max_bases=1000, n_parts=4, part=4) == capi.KMA_EINVAL
     assert _plan_rc(k=31, max_bases=1000, load_factor=0.99) == capi.KMA_EINVAL
 
 

@@ -180,9 +180,10 @@ def test_multiple_count_calls(gpu, plain):
 @pytest.mark.parametrize("shape", [
     dict(block_threads=128, windows_per_thread=1),
     dict(block_threads=256, windows_per_thread=8, warp_aggregate=True),
-    dict(block_threads=1024, windows_per_thread=2, ctas_per_sm=1),
-    dict(block_threads=512, windows_per_thread=16, load_factor=0.85),
-    dict(expected_distinct=50_000, bloom_fpr=0.3, table_capacity=4_000_000),  # tiny, saturated Bloom
+    dict(block_threads=64, windows_per_thread=2, ctas_per_sm=1),
+    dict(block_threads=224, windows_per_thread=4, slot_prefetch=2),
+    dict(block_threads=160, windows_per_thread=8, table_capacity=1_300_000),  # load ~0.85
+    dict(expected_distinct=50_000, bloom_fpr=0.3, table_capacity=9_000_000),  # saturated Bloom: ~all 4.4 M keys inserted
     dict(expected_distinct=200_000_000, bloom_fpr=0.001),  # huge filter
 ])
 def test_results_independent_of_tuning(gpu, plain, shape):
@@ -208,6 +209,18 @@ def test_table_full_is_reported(gpu, plain):
     got = count_kmers(rs.seq, rs.qual, rs.offsets, k=31, table_capacity=300_000,
                       expected_distinct=rs.n_bases).sorted()
     assert_same(got, want, "after EFULL retry")
+
+
+def test_bounded_wait_reports_timeout(gpu):
+    """The packing kernel's wait for its staging copies is bounded: with fault injection the
+    copies are never issued, the wait gives up, and the host sees KMA_ETIMEOUT; the context
+    stays usable for the next handle."""
+    from paper_1705_11147_gb300 import KMA_ETIMEOUT, KmaError
+    rs = synth.workload("plain_1m", scale=0.05)
+    with pytest.raises(KmaError) as ei:
+        run_gpu(gpu, rs, fault_inject=1)
+    assert ei.value.code == KMA_ETIMEOUT
+    assert_same(run_gpu(gpu, rs), oracle.run_readset(rs), "after timeout")
 
 
 def test_reset_and_reuse(gpu, plain):
