@@ -47,6 +47,8 @@ extern "C" {
                               the read-packing kernel) gave up: no partial result */
 #define KMA_EOVERFLOW (-6) /* a 32-bit k-mer counter would have wrapped */
 #define KMA_ECUDA (-7)     /* a CUDA runtime call failed (cudaGetLastError text via strerror) */
+#define KMA_ETOOLARGE (-8) /* input larger than the fixed scratch of the allocation-free entry
+                              point (KMA_NOALLOC_MAX_BASES / KMA_NOALLOC_MAX_READS) */
 
 #define KMA_CODE_X 4
 #define KMA_CODE_F 5
@@ -226,6 +228,37 @@ int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uin
  * Synchronises hs[0]'s stream. Errors as kmer_analysis_finalize; the first failing
  * handle's code is returned and the others are still finalized. */
 int kmer_analysis_finalize_batch(kma_handle* const* hs, uint32_t n, kma_result* out);
+
+/* ---- Allocation-free counting for small read sets --------------------------------------
+ * The paper has no counterpart: this entry point serves callers that must not allocate
+ * device memory when they count, for example code that reserves a fixed memory budget at
+ * start-up and forbids later allocations, or a plugin inside a host framework that owns
+ * every device allocation. It runs the same kernels as create/count/finalize (exact counting
+ * without the Bloom filter, which gives the same records) in one call and allocates nothing:
+ * its working memory (packed reads, hash table, status words) is a fixed file-scope device
+ * array of about 34 MB that every GPU loading the library holds until the process exits.
+ *
+ * Inputs (seq, qual, offsets: read r is seq[offsets[r] .. offsets[r+1]), n_bases must equal
+ * offsets[n_reads] - offsets[0]) and outputs (keys[capacity][2], counts[capacity],
+ * ext[capacity][8], codes[capacity][2], same layout as kma_result) are device pointers
+ * owned by the caller; *n_out (host) receives the number of records, also when it exceeds
+ * `capacity` (then KMA_EFULL is returned and the arrays hold the first `capacity` records in
+ * unspecified order). params->k, canonical, min_depth, min_ext_count, qual_threshold and
+ * qual_offset are used; the sizing and launch-shape fields are ignored.
+ * Limits: n_bases <= KMA_NOALLOC_MAX_BASES and n_reads <= KMA_NOALLOC_MAX_READS, otherwise
+ * KMA_ETOOLARGE and nothing runs. The call synchronises `cuda_stream` before it returns.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any CUDA stream capture. All calls share the array and it keeps
+ * the previous call's contents (each call clears what it needs): calls whose GPU work can
+ * overlap, on different streams or from unsynchronised threads, race on it. */
+#define KMA_NOALLOC_MAX_BASES 262144
+#define KMA_NOALLOC_MAX_READS 262144
+
+int kmer_analysis_count_small_noalloc(const kma_params* params, const char* seq, const char* qual,
+                                      const uint64_t* offsets, uint64_t n_reads, uint64_t n_bases,
+                                      uint64_t* keys, uint32_t* counts, uint32_t* ext,
+                                      uint8_t* codes, uint64_t capacity, uint64_t* n_out,
+                                      void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -19,6 +19,9 @@ KMA_ESTATE = -4
 KMA_ETIMEOUT = -5
 KMA_EOVERFLOW = -6
 KMA_ECUDA = -7
+KMA_ETOOLARGE = -8
+KMA_NOALLOC_MAX_BASES = 262144
+KMA_NOALLOC_MAX_READS = 262144
 KMA_CODE_X = 4
 KMA_CODE_F = 5
 KMA_MAX_BATCH = 64
@@ -77,6 +80,8 @@ _SIGS = {
     "kmer_analysis_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "kmer_analysis_count_batch": ([ctypes.POINTER(vp), ctypes.POINTER(kma_reads), u32], ctypes.c_int),
     "kmer_analysis_finalize_batch": ([ctypes.POINTER(vp), u32, ctypes.POINTER(kma_result)], ctypes.c_int),
+    "kmer_analysis_count_small_noalloc": ([ctypes.POINTER(kma_params), vp, vp, vp, u64, u64, vp, vp,
+                                           vp, vp, u64, ctypes.POINTER(u64), vp], ctypes.c_int),
 }
 
 _LIB = None

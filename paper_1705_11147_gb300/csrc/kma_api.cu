@@ -850,6 +850,7 @@ const char* kmer_analysis_strerror(int code) {
     case KMA_ETIMEOUT: return "device wait timed out";
     case KMA_EOVERFLOW: return "k-mer counter overflow";
     case KMA_ECUDA: return g_last_cuda_error.empty() ? "CUDA error" : g_last_cuda_error.c_str();
+    case KMA_ETOOLARGE: return "input exceeds the allocation-free entry point's fixed scratch limits";
     default: return "unknown error";
   }
 }
