@@ -252,6 +252,8 @@ def run_ours(args, ws, rank, local):
     offs = torch.from_numpy(rs.offsets.astype(np.int64)).to(dev)
     stream = torch.cuda.current_stream(dev)
     prm = make_handle_params(rs, n_parts=ws, part=rank, **args.tuning)
+    from paper_1705_11147_gb300 import plan as _plan
+    plan_used = _plan(prm)
     ka = KmerAnalysis(prm, stream=stream)
 
     # query set: 1 M k-mers present in the result + 1 M random k-mers (mostly absent)
@@ -337,7 +339,8 @@ def run_ours(args, ws, rank, local):
                       "l2": "inputs (12 GB of reads, 33 GB table) far larger than L2; no flush"},
            "roofline": roof, "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
            "tuning": {k2: getattr(prm, k2) for k2 in ("block_threads", "windows_per_thread", "ctas_per_sm",
-                                                      "warp_aggregate", "slot_prefetch")},
+                                                      "warp_aggregate", "slot_prefetch", "partitions")}
+                     | {"partitions_used": int(plan_used.partitions)},
            "clocks": clk, "generation_s": round(t_gen, 1)}
     if e2e:
         out["e2e"] = e2e
@@ -460,6 +463,7 @@ def main():
     for kv in args.tune:
         key, val = kv.split("=", 1)
         args.tuning[key] = float(val) if key == "load_factor" else int(val)
+    args.tuning = {k: v for k, v in args.tuning.items()}
     ws, rank, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, ws, rank)

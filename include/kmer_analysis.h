@@ -94,17 +94,26 @@ typedef struct {
   uint32_t fault_inject;      /* testing only. 0: off. 1: the read-packing kernel waits for
                                  staging copies it never issued, with a short poll limit, so
                                  its bounded wait gives up and the handle reports KMA_ETIMEOUT */
+  uint32_t partitions;        /* on-chip owner-computes partitions (Section 5.1's owner map on
+                                 one GPU): the Bloom filter and table are split by a hash into
+                                 P parts, windows are first written to per-part record buckets,
+                                 and the buckets are counted part by part so one part's filter
+                                 and table stay in L2. 0: automatic (P > 1 when filter + table
+                                 exceed 256 MB, about 48 MB per part); 1: one table, windows
+                                 counted in place; P >= 2: that many parts (<= 4096). Results
+                                 do not depend on it. */
 } kma_params;
 
 /* Sizes derived from a kma_params (pure host arithmetic, no GPU needed). */
 typedef struct {
   uint64_t bloom_words;    /* 64-bit words of the blocked Bloom filter (0 without Bloom) */
   uint32_t bloom_hashes;   /* bits set per k-mer, all inside one 64-bit word */
-  uint32_t reserved;
+  uint32_t partitions;     /* on-chip partitions (1: one table) */
   double bloom_fpr_est;    /* predicted false-positive rate at expected_distinct k-mers */
   uint64_t table_slots;    /* hash-table slots, 64 bytes each */
   uint64_t arena_positions;/* packed positions: bases + one separator per read + padding */
-  uint64_t device_bytes;   /* device memory a handle holds (all buffers) */
+  uint64_t device_bytes;   /* device memory a handle holds (all buffers; with partitions,
+                              including per-window records for max_bases windows) */
 } kma_plan;
 
 /* Result of finalize. Pointers are device memory owned by the handle, valid until the
@@ -194,6 +203,7 @@ typedef struct {
 #define KMA_KERNEL_CLASSIFY 3
 #define KMA_KERNEL_QUERY 4
 #define KMA_KERNEL_INIT 5      /* table initialisation on create / reset */
+#define KMA_KERNEL_SCATTER 7   /* partitioned mode: windows -> per-partition record buckets */
 
 int kmer_analysis_set_profiling(kma_handle* h, int enable);
 int kmer_analysis_timings(kma_handle* h, kma_timings* out, int reset);

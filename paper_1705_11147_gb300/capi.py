@@ -37,11 +37,11 @@ class kma_params(ctypes.Structure):
                 ("load_factor", dbl), ("staging_bytes", u64),
                 ("block_threads", u32), ("windows_per_thread", u32), ("ctas_per_sm", u32),
                 ("warp_aggregate", u32), ("n_parts", u32), ("part", u32),
-                ("slot_prefetch", u32), ("fault_inject", u32)]
+                ("slot_prefetch", u32), ("fault_inject", u32), ("partitions", u32)]
 
 
 class kma_plan(ctypes.Structure):
-    _fields_ = [("bloom_words", u64), ("bloom_hashes", u32), ("reserved", u32),
+    _fields_ = [("bloom_words", u64), ("bloom_hashes", u32), ("partitions", u32),
                 ("bloom_fpr_est", dbl), ("table_slots", u64), ("arena_positions", u64),
                 ("device_bytes", u64)]
 
@@ -56,7 +56,7 @@ class kma_timings(ctypes.Structure):
                 ("first_sightings", u64)]
 
 
-KERNEL_KINDS = ("pack", "pass", "recount", "classify", "query", "init")
+KERNEL_KINDS = ("pack", "pass", "recount", "classify", "query", "init", "unused", "scatter")
 
 
 class kma_reads(ctypes.Structure):

@@ -91,7 +91,13 @@ struct Derived {
   kma_plan plan;
   u64 codes_words, bit_words, mark_words;
   u64 staging;
+  unsigned P;      // on-chip partitions (1: one table)
+  u64 Wp, Sp;      // Bloom words / table slots per partition
+  u64 rec_bytes;   // bytes per record in partitioned mode
 };
+
+constexpr u64 kAutoPartitionAbove = 256ull << 20;  // filter + table bytes
+constexpr u64 kPartitionTarget = 48ull << 20;      // filter + table bytes per partition
 
 int check_params(const kma_params* p) {
   if (!p) return KMA_EINVAL;
@@ -109,6 +115,7 @@ int check_params(const kma_params* p) {
     return KMA_EINVAL;
   if (p->slot_prefetch > 2) return KMA_EINVAL;
   if (p->fault_inject > 1) return KMA_EINVAL;
+  if (p->partitions > kMaxPartitions) return KMA_EINVAL;
   if (p->n_parts > 1 && p->part >= p->n_parts) return KMA_EINVAL;
   return KMA_OK;
 }
@@ -131,6 +138,30 @@ int derive(const kma_params* p, Derived& d) {
     const double lf = p->load_factor > 0 ? p->load_factor : 0.5;
     d.plan.table_slots = (u64)std::ceil(keys / lf) + 64;
   }
+  // on-chip partitions: each part's Bloom sub-filter and sub-table sized for L2
+  {
+    const u64 W = d.plan.bloom_words, S = d.plan.table_slots;
+    const u64 bytes = W * 8 + S * sizeof(Slot);
+    u64 P = p->partitions;
+    if (P == 0) P = bytes > kAutoPartitionAbove ? (bytes + kPartitionTarget - 1) / kPartitionTarget : 1;
+    if (P > kMaxPartitions) P = kMaxPartitions;
+    if (P < 1) P = 1;
+    d.P = (unsigned)P;
+    d.Wp = (W + P - 1) / P;
+    d.Sp = (S + P - 1) / P;
+    if (P > 1) {
+      if (d.Sp < 64) d.Sp = 64;
+      d.plan.bloom_words = W ? d.Wp * P : 0;
+      d.plan.table_slots = d.Sp * P;
+    } else {
+      d.Wp = W;
+      d.Sp = S;
+    }
+    d.plan.partitions = d.P;
+    d.rec_bytes = (p->k > 32 ? 16 : 8) + 1;
+  }
+  // bit slices of the key hash address at most 2^32 Bloom words and 2^32 slots per partition
+  if (d.plan.bloom_words >= (1ull << 32) || d.Sp >= (1ull << 32)) return KMA_EINVAL;
   const u64 reads = p->max_reads ? p->max_reads : p->max_bases / 32 + 1;
   const u64 pos = ((p->max_bases + reads + kArenaSlack + 63) / 64) * 64;
   d.plan.arena_positions = pos;
@@ -141,6 +172,7 @@ int derive(const kma_params* p, Derived& d) {
   d.plan.device_bytes = d.codes_words * 8 + 2 * d.bit_words * 8 + d.mark_words * 4 +
                         d.plan.bloom_words * 8 + d.plan.table_slots * sizeof(Slot) +
                         sizeof(DevStatus) + 2 * (2 * d.staging + (d.staging / 16 + 2) * 8);
+  if (d.P > 1) d.plan.device_bytes += (p->max_bases + p->max_bases / 16) * d.rec_bytes;
   return KMA_OK;
 }
 
@@ -201,6 +233,11 @@ struct kma_handle {
   u64 q_used = 0, reads_used = 0, bases_used = 0;
   bool finalized = false;
   bool failed = false;
+
+  // partitioned mode: per-partition histogram / cursors and the record buckets of each
+  // count() batch (kept until finalize has recounted them)
+  struct RecBatch { void* keys; unsigned char* info; u64* fill; u64 cap, ocap; };
+  std::vector<RecBatch> rec_batches;
 
   u64* out_keys = nullptr;
   unsigned* out_counts = nullptr;
@@ -271,7 +308,17 @@ int timed_launch(kma_handle* h, int kind, cudaStream_t stream, bool has_work, F&
   return KMA_OK;
 }
 
+void free_records(kma_handle* h) {
+  for (auto& b : h->rec_batches) {
+    if (b.keys) cudaFreeAsync(b.keys, h->stream);
+    if (b.info) cudaFreeAsync(b.info, h->stream);
+    if (b.fill) cudaFreeAsync(b.fill, h->stream);
+  }
+  h->rec_batches.clear();
+}
+
 void free_all(kma_handle* h) {
+  free_records(h);
   dfree(h, h->codes); dfree(h, h->inv); dfree(h, h->hq); dfree(h, h->marks);
   dfree(h, h->bloom); dfree(h, h->table); dfree(h, h->status);
   for (int i = 0; i < 2; ++i) { dfree(h, h->stage_seq[i]); dfree(h, h->stage_qual[i]); dfree(h, h->stage_offs[i]); }
@@ -293,6 +340,7 @@ void free_all(kma_handle* h) {
 }
 
 int clear_state(kma_handle* h) {
+  free_records(h);
   KMA_CUDA(cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->stream));
   if (h->bloom) KMA_CUDA(cudaMemsetAsync(h->bloom, 0, h->d.plan.bloom_words * 8, h->stream));
   int rc = timed_launch(h, KMA_KERNEL_INIT, h->stream, h->d.plan.table_slots > 0,
@@ -373,6 +421,76 @@ int reserve_batch(kma_handle* h, u64 n_reads, u64 n_bases, PackDesc& pd, u64& q0
   return KMA_OK;
 }
 
+PartGeom part_geom(kma_handle* h) {
+  PartGeom g;
+  std::memset(&g, 0, sizeof(g));
+  g.bloom = h->bloom;
+  g.table = h->table;
+  g.status = h->status;
+  g.Wp = h->d.Wp;
+  g.Sp = h->d.Sp;
+  g.P = h->d.P;
+  g.bloom_h = h->d.plan.bloom_hashes;
+  g.k = h->p.k;
+  g.canonical = h->p.canonical;
+  g.n_parts = h->p.n_parts > 1 ? h->p.n_parts : 1;
+  g.part = h->p.n_parts > 1 ? h->p.part : 0;
+  return g;
+}
+
+// First pass over the windows [q0, q0 + n_pos) of one packed batch (n_reads reads, n_bases
+// bases) on stream `st`. One table: Bloom test-and-set (or counting) in place. Partitions:
+// scatter into per-partition record buckets, then the record pass part by part; the buckets
+// are kept for the recount in finalize. Nothing here waits for the GPU.
+int first_pass(kma_handle* h, u64 q0, u64 n_pos, u64 n_reads, u64 n_bases, cudaStream_t st) {
+  const unsigned mode = h->p.use_bloom ? kModeBloom : kModeCount;
+  if (h->d.P <= 1) {
+    PassBatch b;
+    std::memset(&b, 0, offsetof(PassBatch, d) + sizeof(PassDesc));
+    b.n = 1;
+    b.prefetch = h->prefetch;
+    b.d[0] = pass_desc(h, mode, q0, q0 + n_pos);
+    const u64 tile = (u64)h->shape.block_threads * h->shape.windows_per_thread;
+    b.d[0].tile_begin = 0;
+    b.total_tiles = (n_pos + tile - 1) / tile;
+    return timed_launch(h, KMA_KERNEL_PASS, st, b.total_tiles > 0,
+                        [&] { return launch_pass(b, h->shape, h->agg, st); });
+  }
+  const PartGeom g = part_geom(h);
+  PartWindows w;
+  w.codes = h->codes; w.inv = h->inv; w.hq = h->hq;
+  w.q0 = q0; w.q1 = q0 + n_pos;
+  const u64 P = h->d.P, k = h->p.k;
+  // Bucket capacity from the window count of reads of length >= k (exact for such reads);
+  // shorter reads, hash imbalance and repeated k-mers spill into the overflow area.
+  const u64 w_est = n_bases > (k - 1) * n_reads ? n_bases - (k - 1) * n_reads : 0;
+  u64 cap = (u64)((double)w_est / (double)P * 1.05) + 64;
+  u64 ocap = n_pos / 16 + 65536;
+  if (P * cap < n_bases) ocap = std::max(ocap, n_bases - P * cap + n_pos / 64);
+  if (cap >= (1ull << 32)) return KMA_EINVAL;  // more partitions needed for this batch size
+  const u64 total = P * cap + ocap;
+  kma_handle::RecBatch rb{nullptr, nullptr, nullptr, cap, ocap};
+  const size_t kb = (size_t)total * (k > 32 ? 16 : 8);
+  cudaError_t e = cudaMallocFromPoolAsync(&rb.keys, kb, h->pool, st);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&rb.info, (size_t)total, h->pool, st);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&rb.fill, (size_t)(P + 1) * 8, h->pool, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (rb.keys) cudaFreeAsync(rb.keys, st);
+    if (rb.info) cudaFreeAsync(rb.info, st);
+    return e == cudaErrorMemoryAllocation ? KMA_ENOMEM : cuda_fail(e, "record buckets");
+  }
+  h->rec_batches.push_back(rb);
+  KMA_CUDA(cudaMemsetAsync(rb.fill, 0, (size_t)(P + 1) * 8, st));
+  PartRecords r;
+  r.keys = rb.keys; r.info = rb.info; r.cap = cap; r.ocap = ocap; r.fill = rb.fill;
+  int rc = timed_launch(h, KMA_KERNEL_SCATTER, st, n_pos > 0,
+                        [&] { return launch_part_scatter(g, w, r, st, h->num_sms); });
+  if (rc) return rc;
+  return timed_launch(h, KMA_KERNEL_PASS, st, n_pos > 0,
+                      [&] { return launch_part_pass(g, r, mode, st, h->num_sms); });
+}
+
 int run_pack_and_pass(kma_handle* h, const PackDesc& pd) {
   PackBatch pb;
   std::memset(&pb, 0, offsetof(PackBatch, d) + sizeof(PackDesc));
@@ -384,16 +502,7 @@ int run_pack_and_pass(kma_handle* h, const PackDesc& pd) {
   int rc = timed_launch(h, KMA_KERNEL_PACK, h->stream, pb.total_chunks > 0,
                         [&] { return launch_pack(pb, h->stream, h->num_sms); });
   if (rc) return rc;
-  PassBatch b;
-  std::memset(&b, 0, offsetof(PassBatch, d) + sizeof(PassDesc));
-  b.n = 1;
-  b.prefetch = h->prefetch;
-  b.d[0] = pass_desc(h, h->p.use_bloom ? kModeBloom : kModeCount, pd.q0, pd.q0 + pd.n_pos);
-  const u64 tile = (u64)h->shape.block_threads * h->shape.windows_per_thread;
-  b.d[0].tile_begin = 0;
-  b.total_tiles = (pd.n_pos + tile - 1) / tile;
-  return timed_launch(h, KMA_KERNEL_PASS, h->stream, b.total_tiles > 0,
-                      [&] { return launch_pass(b, h->shape, h->agg, h->stream); });
+  return first_pass(h, pd.q0, pd.n_pos, pd.n_reads, pd.n_bases, h->stream);
 }
 
 int ensure_output(kma_handle* h, u64 need) {
@@ -474,6 +583,7 @@ int kmer_analysis_create(const kma_params* params, void* cuda_stream, kma_handle
   }
   e = cudaMallocHost((void**)&h->host_status, sizeof(DevStatus));
   if (e != cudaSuccess) { free_all(h); delete h; return cuda_fail(e, "cudaMallocHost"); }
+
   std::memset(h->host_status, 0, sizeof(DevStatus));
   if ((rc = clear_state(h))) { free_all(h); delete h; return rc; }
   *out = h;
@@ -557,16 +667,7 @@ int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual, const 
                            [&] { return launch_pack(pb, h->stream, h->num_sms); })))
       return rc;
     KMA_CUDA(cudaEventRecord(h->consumed[b], h->stream));
-    PassBatch pb2;
-    std::memset(&pb2, 0, offsetof(PassBatch, d) + sizeof(PassDesc));
-    pb2.n = 1;
-    pb2.prefetch = h->prefetch;
-    pb2.d[0] = pass_desc(h, h->p.use_bloom ? kModeBloom : kModeCount, q0, q0 + n_pos);
-    const u64 tile = (u64)h->shape.block_threads * h->shape.windows_per_thread;
-    pb2.total_tiles = (n_pos + tile - 1) / tile;
-    if ((rc = timed_launch(h, KMA_KERNEL_PASS, h->stream, true,
-                           [&] { return launch_pass(pb2, h->shape, h->agg, h->stream); })))
-      return rc;
+    if ((rc = first_pass(h, q0, n_pos, r1 - r0, nb, h->stream))) return rc;
     r0 = r1;
   }
   // Host buffers may be reused once the call returns: wait for the copies.
@@ -601,7 +702,7 @@ static int finalize_many(kma_handle* const* hs, uint32_t n, kma_result* out) {
   u64 tiles = 0;
   for (uint32_t i = 0; i < n; ++i) {
     kma_handle* h = hs[i];
-    if (!h->p.use_bloom || h->q_used == 0) continue;
+    if (!h->p.use_bloom || h->q_used == 0 || h->d.P > 1) continue;
     PassDesc d = pass_desc(h, kModeRecount, 0, h->q_used);
     d.tile_begin = tiles;
     tiles += (h->q_used + tile - 1) / tile;
@@ -612,6 +713,18 @@ static int finalize_many(kma_handle* const* hs, uint32_t n, kma_result* out) {
     int rc = timed_launch(h0, KMA_KERNEL_RECOUNT, h0->stream, pb.n > 0 && tiles > 0,
                           [&] { return launch_pass(pb, h0->shape, h0->agg, h0->stream); });
     if (rc) return rc;
+  }
+  for (uint32_t i = 0; i < n; ++i) {  // partitioned handles: recount their record buckets
+    kma_handle* h = hs[i];
+    if (!h->p.use_bloom || h->d.P <= 1) continue;
+    const PartGeom g = part_geom(h);
+    for (auto& rb : h->rec_batches) {
+      PartRecords r;
+      r.keys = rb.keys; r.info = rb.info; r.cap = rb.cap; r.ocap = rb.ocap; r.fill = rb.fill;
+      int rc = timed_launch(h0, KMA_KERNEL_RECOUNT, h0->stream, true,
+                            [&] { return launch_part_pass(g, r, kModeRecount, h0->stream, h0->num_sms); });
+      if (rc) return rc;
+    }
   }
   // 2. statuses -> output capacities
   for (uint32_t i = 0; i < n; ++i) {
@@ -651,8 +764,14 @@ static int finalize_many(kma_handle* const* hs, uint32_t n, kma_result* out) {
                           [&] { return launch_classify(cb, h0->stream, h0->num_sms); });
     if (rc) return rc;
   }
-  for (uint32_t i = 0; i < n; ++i)
+  for (uint32_t i = 0; i < n; ++i) {
     if (ok[i]) KMA_CUDA(cudaMemcpyAsync(hs[i]->host_status, hs[i]->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, h0->stream));
+    // the record buckets are not needed after the recount
+    cudaStream_t saved = hs[i]->stream;
+    hs[i]->stream = h0->stream;
+    free_records(hs[i]);
+    hs[i]->stream = saved;
+  }
   KMA_CUDA(cudaStreamSynchronize(h0->stream));
   for (uint32_t i = 0; i < n; ++i) {
     kma_handle* h = hs[i];
@@ -690,6 +809,8 @@ int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uin
   PackBatch pk;
   std::memset(&pk, 0, sizeof(pk));
   set_pack_waits(h0, pk);
+  struct Later { kma_handle* h; u64 q0, n_pos, n_reads, n_bases; };
+  std::vector<Later> part_later;
   PassBatch ps;
   std::memset(&ps, 0, sizeof(ps));
   ps.prefetch = h0->prefetch;
@@ -709,6 +830,10 @@ int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uin
     pd.chunk_begin = words;
     words += (n_pos / 64 + kPackChunkWords - 1) / kPackChunkWords;
     pk.d[pk.n++] = pd;
+    if (h->d.P > 1) {  // partitioned: its own histogram/scatter/record pass after the packing
+      part_later.push_back({h, q0, n_pos, reads[i].n_reads, reads[i].n_bases});
+      continue;
+    }
     PassDesc d = pass_desc(h, h->p.use_bloom ? kModeBloom : kModeCount, q0, q0 + n_pos);
     d.tile_begin = tiles;
     tiles += (n_pos + tile - 1) / tile;
@@ -719,8 +844,12 @@ int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uin
   int rc = timed_launch(h0, KMA_KERNEL_PACK, h0->stream, pk.n > 0 && words > 0,
                         [&] { return launch_pack(pk, h0->stream, h0->num_sms); });
   if (rc) return rc;
-  return timed_launch(h0, KMA_KERNEL_PASS, h0->stream, ps.n > 0 && tiles > 0,
-                      [&] { return launch_pass(ps, h0->shape, h0->agg, h0->stream); });
+  rc = timed_launch(h0, KMA_KERNEL_PASS, h0->stream, ps.n > 0 && tiles > 0,
+                    [&] { return launch_pass(ps, h0->shape, h0->agg, h0->stream); });
+  if (rc) return rc;
+  for (auto& l : part_later)
+    if ((rc = first_pass(l.h, l.q0, l.n_pos, l.n_reads, l.n_bases, h0->stream))) return rc;
+  return KMA_OK;
 }
 
 int kmer_analysis_copy_result(kma_handle* h, uint64_t* keys, uint32_t* counts, uint32_t* ext,
@@ -749,7 +878,7 @@ int kmer_analysis_query(kma_handle* h, const uint64_t* keys, uint64_t n, uint32_
   const unsigned min_ext = h->p.min_ext_count ? h->p.min_ext_count : 1;
   if (on_device) {
     return timed_launch(h, KMA_KERNEL_QUERY, h->stream, true, [&] {
-      return launch_query(h->table, h->d.plan.table_slots, h->p.k, h->p.canonical, h->p.min_depth,
+      return launch_query(h->table, h->d.Sp, h->d.P, h->p.k, h->p.canonical, h->p.min_depth,
                           min_ext, (const u64*)keys, n, counts, ext, codes, h->status, h->stream);
     });
   }
@@ -765,7 +894,7 @@ int kmer_analysis_query(kma_handle* h, const uint64_t* keys, uint64_t n, uint32_
   cudaError_t e = cudaMemcpyAsync(dk, keys, n * 16, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) {
     rc = timed_launch(h, KMA_KERNEL_QUERY, h->stream, true, [&] {
-      return launch_query(h->table, h->d.plan.table_slots, h->p.k, h->p.canonical, h->p.min_depth,
+      return launch_query(h->table, h->d.Sp, h->d.P, h->p.k, h->p.canonical, h->p.min_depth,
                           min_ext, dk, n, dc, de, dcode, h->status, h->stream);
     });
     if (rc) { dfree(h, dk); dfree(h, dc); dfree(h, de); dfree(h, dcode); return rc; }

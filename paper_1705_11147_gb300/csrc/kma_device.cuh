@@ -1,0 +1,304 @@
+// Device helpers shared by the library's kernels (not part of the C ABI): hashing, 2-bit
+// k-mer words, window extraction from the packed-read arena, and the hash-table operations.
+#pragma once
+#include "kma_internal.cuh"
+
+namespace kma {
+
+typedef unsigned long long u64;
+typedef unsigned __int128 u128;
+
+// ------------------------------------------------------------------ hashing
+
+// 64-bit finaliser of MurmurHash3 (Appleby).
+__device__ __forceinline__ u64 fmix64(u64 x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+__device__ __forceinline__ u64 key_hash(u64 lo, u64 hi) {
+  return fmix64(lo ^ fmix64(hi + 0x9e3779b97f4a7c15ull));
+}
+
+// Everything derived from the 64-bit key hash h uses cheap 32-bit slices of h and of one more
+// product g = h * phi (golden-ratio constant), instead of further 64-bit mixes:
+//   on-chip partition   high 32 bits of h     (part_of)
+//   Bloom word          low 32 bits of h      (bloom_index; the filter has < 2^32 words)
+//   table slot          high 32 bits of g     (table_index; < 2^32 slots per partition)
+//   Bloom bit positions 6-bit fields of g     (bloom_mask)
+__device__ __forceinline__ u64 scramble(u64 h) { return h * 0x9e3779b97f4a7c15ull; }
+__device__ __forceinline__ u64 table_index(u64 h, u64 slots) {
+  return __umulhi((unsigned)(scramble(h) >> 32), (unsigned)slots);
+}
+__device__ __forceinline__ u64 bloom_index(u64 h, u64 words) {
+  return __umulhi((unsigned)h, (unsigned)words);
+}
+// Owner GPU of a k-mer (multi-GPU owner-computes), independent of the bits above.
+__device__ __forceinline__ unsigned owner_of(u64 h, unsigned n_parts) {
+  return __umulhi((unsigned)(fmix64(h ^ 0x9fb21c651e98df25ull) >> 32), n_parts);
+}
+
+// On-chip partition (partitioned mode) of a k-mer with hash h, 0 .. P-1.
+__device__ __forceinline__ unsigned part_of(u64 h, unsigned P) {
+  return __umulhi((unsigned)(h >> 32), P);
+}
+
+__device__ __forceinline__ u64 bloom_mask(u64 h, unsigned nbits) {
+  const u64 g = scramble(h);
+  u64 m = 0;
+  for (unsigned i = 0; i < nbits; ++i) m |= 1ull << ((g >> (6 * i)) & 63);
+  return m;
+}
+
+// L2 cache policy for data read or written once (record streams): evict first, so the
+// partition's Bloom sub-filter and sub-table stay resident.
+__device__ __forceinline__ u64 policy_evict_first() {
+  u64 pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ ulonglong2 ld_stream(const ulonglong2* p, u64 pol) {
+  ulonglong2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+               : "=l"(v.x), "=l"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ u64 ld_stream(const u64* p, u64 pol) {
+  u64 v;
+  asm volatile("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ unsigned ld_stream(const unsigned char* p, u64 pol) {
+  unsigned v;
+  asm volatile("ld.global.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_stream(ulonglong2* p, ulonglong2 v, u64 pol) {
+  asm volatile("st.global.L2::cache_hint.v2.u64 [%0], {%1, %2}, %3;" ::"l"(p), "l"(v.x), "l"(v.y), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st_stream(u64* p, u64 v, u64 pol) {
+  asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_stream(unsigned char* p, unsigned v, u64 pol) {
+  asm volatile("st.global.L2::cache_hint.u8 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+
+// ------------------------------------------------------------------ 2-bit words
+
+// Reverse the order of the 32 two-bit groups of x.
+__device__ __forceinline__ u64 rev2(u64 x) {
+  x = __brevll(x);
+  return ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
+}
+
+// Reverse complement of a k-mer held in the low 2k bits of (hi:lo).
+__device__ __forceinline__ void revcomp(u64 lo, u64 hi, unsigned k, u64& rlo, u64& rhi) {
+  u128 r = ((u128)rev2(lo) << 64) | (u128)rev2(hi);
+  r = ~r;
+  r >>= (128 - 2 * k);
+  rlo = (u64)r;
+  rhi = (u64)(r >> 64);
+}
+
+__device__ __forceinline__ unsigned code_at(const u64* codes, u64 p) {
+  return (unsigned)(codes[p >> 5] >> (62 - 2 * (p & 31))) & 3u;
+}
+
+__device__ __forceinline__ unsigned bit_at(const u64* bits, u64 p) {
+  return (unsigned)(bits[p >> 6] >> (63 - (p & 63))) & 1u;
+}
+
+struct Window {
+  u64 lo, hi;        // canonical key
+  unsigned lb, rb;   // extension bases in the key's orientation
+  bool lu, ru;       // usable (exists, A/C/G/T, Phred >= threshold)
+};
+
+// Window starting at arena position q: returns false if any of its k positions is invalid.
+__device__ __forceinline__ bool load_window(const u64* codes, const u64* inv, const u64* hq,
+                                            unsigned k, unsigned canonical, u64 q, Window& w) {
+  const u64 v = q >> 6;
+  const unsigned t = (unsigned)(q & 63);
+  u64 x = inv[v] << t;
+  if (t) x |= inv[v + 1] >> (64 - t);
+  if (x >> (64 - k)) return false;
+
+  const u64 wi = q >> 5;
+  const unsigned s = 2 * (unsigned)(q & 31);
+  const u64 a = codes[wi], b = codes[wi + 1], c = codes[wi + 2];
+  u128 top = ((u128)a << 64) | (u128)b;
+  if (s) top = (top << s) | (u128)(c >> (64 - s));
+  const u128 fw = top >> (128 - 2 * k);
+  const u64 flo = (u64)fw, fhi = (u64)(fw >> 64);
+
+  // Extension bases: position q-1 (before) and q+k (after).
+  const bool bu = q > 0 && bit_at(hq, q - 1);
+  const bool au = bit_at(hq, q + k) != 0;
+  const unsigned bb = q > 0 ? code_at(codes, q - 1) : 0u;
+  const unsigned ab = (unsigned)(top >> (126 - 2 * k)) & 3u;  // the base right after the window
+
+  u64 rlo, rhi;
+  revcomp(flo, fhi, k, rlo, rhi);
+  const bool forward = !canonical || (fhi < rhi) || (fhi == rhi && flo <= rlo);
+  if (forward) {
+    w.lo = flo; w.hi = fhi;
+    w.lb = bb; w.lu = bu;
+    w.rb = ab; w.ru = au;
+  } else {
+    w.lo = rlo; w.hi = rhi;
+    w.lb = 3u - ab; w.lu = au;
+    w.rb = 3u - bb; w.ru = bu;
+  }
+  return true;
+}
+
+__device__ __forceinline__ bool load_window(const PassDesc& D, u64 q, Window& w) {
+  return load_window(D.codes, D.inv, D.hq, D.k, D.canonical, q, w);
+}
+
+// ------------------------------------------------------------------ table
+
+__device__ __forceinline__ void cas128(Slot* s, u64 cmp_lo, u64 cmp_hi, u64 new_lo, u64 new_hi,
+                                       u64& old_lo, u64& old_hi) {
+  asm volatile(
+      "{\n\t"
+      ".reg .b128 d, c, n;\n\t"
+      "mov.b128 c, {%2, %3};\n\t"
+      "mov.b128 n, {%4, %5};\n\t"
+      "atom.global.cas.b128 d, [%6], c, n;\n\t"
+      "mov.b128 {%0, %1}, d;\n\t"
+      "}"
+      : "=l"(old_lo), "=l"(old_hi)
+      : "l"(cmp_lo), "l"(cmp_hi), "l"(new_lo), "l"(new_hi), "l"(s)
+      : "memory");
+}
+
+// Insert-if-absent. Keys are written once (empty -> key) by a 16-byte CAS and never change
+// again. A plain 16-byte load may observe a half-written slot; any value with a word still
+// equal to the empty pattern is therefore resolved by the CAS itself, which is atomic.
+// Returns the slot or nullptr (probe limit reached: the table is full).
+__device__ __forceinline__ Slot* find_or_insert(Slot* table, u64 slots, u64 lo, u64 hi, u64 h,
+                                                bool& inserted) {
+  u64 idx = table_index(h, slots);
+  const u64 limit = slots < kMaxProbe ? slots : kMaxProbe;
+  inserted = false;
+  for (u64 n = 0; n < limit; ++n) {
+    Slot* s = table + idx;
+    const ulonglong2 kv = __ldcg(reinterpret_cast<const ulonglong2*>(s));
+    if (kv.x == lo && kv.y == hi) return s;
+    if (kv.y == kEmpty || kv.x == kEmpty) {
+      u64 olo, ohi;
+      cas128(s, kEmpty, kEmpty, lo, hi, olo, ohi);
+      if (olo == kEmpty && ohi == kEmpty) { inserted = true; return s; }
+      if (olo == lo && ohi == hi) return s;
+    }
+    idx = (idx + 1 == slots) ? 0 : idx + 1;
+  }
+  return nullptr;
+}
+
+// Lookup in a table no thread is modifying. nullptr if absent; sets `full` if the probe
+// limit was reached without finding an empty slot.
+__device__ __forceinline__ const Slot* find(const Slot* table, u64 slots, u64 lo, u64 hi, u64 h,
+                                            bool& full) {
+  u64 idx = table_index(h, slots);
+  const u64 limit = slots < kMaxProbe ? slots : kMaxProbe;
+  full = false;
+  for (u64 n = 0; n < limit; ++n) {
+    const Slot* s = table + idx;
+    const ulonglong2 kv = __ldcg(reinterpret_cast<const ulonglong2*>(s));
+    if (kv.x == lo && kv.y == hi) return s;
+    if (kv.y == kEmpty) return nullptr;
+    idx = (idx + 1 == slots) ? 0 : idx + 1;
+  }
+  full = true;
+  return nullptr;
+}
+
+__device__ __forceinline__ void add_occurrence(Slot* s, const Window& w, unsigned inc,
+                                               DevStatus* st) {
+  const unsigned old = atomicAdd(&s->count, inc);
+  if (old > 0xFFFFFFFFu - inc) atomicOr(&st->flags, kFlagOverflow);
+  if (w.lu) atomicAdd(&s->ext[w.lb], 1u);
+  if (w.ru) atomicAdd(&s->ext[4 + w.rb], 1u);
+}
+
+// Warp-aggregated variant: lanes in `act` holding the same slot merge their count into one
+// atomic, and lanes adding to the same extension counter merge theirs.
+__device__ __forceinline__ void add_occurrence_agg(unsigned act, Slot* s, const Window& w,
+                                                   DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(act, reinterpret_cast<u64>(s));
+  if (lane == __ffs(peers) - 1) {
+    const unsigned inc = __popc(peers);
+    const unsigned old = atomicAdd(&s->count, inc);
+    if (old > 0xFFFFFFFFu - inc) atomicOr(&st->flags, kFlagOverflow);
+  }
+  const unsigned lact = __ballot_sync(act, w.lu);
+  if (w.lu) {
+    unsigned* a = &s->ext[w.lb];
+    const unsigned m = __match_any_sync(lact, reinterpret_cast<u64>(a));
+    if (lane == __ffs(m) - 1) atomicAdd(a, (unsigned)__popc(m));
+  }
+  const unsigned ract = __ballot_sync(act, w.ru);
+  if (w.ru) {
+    unsigned* a = &s->ext[4 + w.rb];
+    const unsigned m = __match_any_sync(ract, reinterpret_cast<u64>(a));
+    if (lane == __ffs(m) - 1) atomicAdd(a, (unsigned)__popc(m));
+  }
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Insert-if-absent continuing from a first probe whose slot (index idx) is already loaded.
+__device__ __forceinline__ Slot* resolve_insert(Slot* table, u64 slots, u64 idx, ulonglong2 kv,
+                                                u64 lo, u64 hi, bool& inserted) {
+  const u64 limit = slots < kMaxProbe ? slots : kMaxProbe;
+  inserted = false;
+  for (u64 n = 0; n < limit; ++n) {
+    Slot* s = table + idx;
+    if (n) kv = __ldcg(reinterpret_cast<const ulonglong2*>(s));
+    if (kv.x == lo && kv.y == hi) return s;
+    if (kv.y == kEmpty || kv.x == kEmpty) {
+      u64 olo, ohi;
+      cas128(s, kEmpty, kEmpty, lo, hi, olo, ohi);
+      if (olo == kEmpty && ohi == kEmpty) { inserted = true; return s; }
+      if (olo == lo && ohi == hi) return s;
+    }
+    idx = (idx + 1 == slots) ? 0 : idx + 1;
+  }
+  return nullptr;
+}
+
+// Lookup (table not being modified) continuing from a loaded first probe.
+__device__ __forceinline__ Slot* resolve_find(Slot* table, u64 slots, u64 idx, ulonglong2 kv,
+                                              u64 lo, u64 hi, bool& full) {
+  const u64 limit = slots < kMaxProbe ? slots : kMaxProbe;
+  full = false;
+  for (u64 n = 0; n < limit; ++n) {
+    Slot* s = table + idx;
+    if (n) kv = __ldcg(reinterpret_cast<const ulonglong2*>(s));
+    if (kv.x == lo && kv.y == hi) return s;
+    if (kv.y == kEmpty) return nullptr;
+    idx = (idx + 1 == slots) ? 0 : idx + 1;
+  }
+  full = true;
+  return nullptr;
+}
+
+__device__ __forceinline__ unsigned side_code(const unsigned* e, unsigned min_ext) {
+  unsigned n = 0, b = 0;
+#pragma unroll
+  for (unsigned j = 0; j < 4; ++j)
+    if (e[j] >= min_ext) { ++n; b = j; }
+  return n == 0 ? 4u : (n >= 2 ? 5u : b);
+}
+
+}  // namespace kma

@@ -133,6 +133,55 @@ struct ClassBatch {
   ClassDesc d[kMaxBatch];
 };
 
+// ---- Partitioned mode ("owner-computes on chip", Section 5.1's k-mer -> owner map) -------
+// The k-mer space is split by a hash into P partitions; partition p owns Bloom words
+// [p*Wp, (p+1)*Wp) and table slots [p*Sp, (p+1)*Sp). Windows are first scattered into
+// per-partition record buckets (streaming writes), then the buckets are processed in order,
+// so the random Bloom/table traffic of one partition stays in L2.
+constexpr unsigned kMaxPartitions = 4096;
+
+// Record info byte: bits 0-1 left base, bit 2 left usable, bits 3-4 right base,
+// bit 5 right usable, bit 7 first sighting (set by the Bloom pass).
+constexpr unsigned char kInfoFirst = 0x80;
+
+struct PartGeom {
+  unsigned long long* bloom;
+  Slot* table;
+  DevStatus* status;
+  unsigned long long Wp;        // Bloom words per partition
+  unsigned long long Sp;        // table slots per partition
+  unsigned int P;
+  unsigned int bloom_h;
+  unsigned int k;
+  unsigned int canonical;
+  unsigned int n_parts;         // multi-GPU owner filter (as PassDesc)
+  unsigned int part;
+};
+
+struct PartWindows {
+  const unsigned long long* codes;
+  const unsigned long long* inv;
+  const unsigned long long* hq;
+  unsigned long long q0, q1;    // window starts of one count() batch (multiples of 64)
+};
+
+// Record buckets of one count() batch: P buckets of `cap` records (bucket p starts at p*cap),
+// then an overflow area of `ocap` records for partitions whose bucket filled up. fill[p]
+// counts the records that were assigned to bucket p (those beyond cap went to the overflow
+// area); fill[P] counts the overflow records.
+struct PartRecords {
+  void* keys;                   // unsigned long long[] (k <= 32) or ulonglong2[]
+  unsigned char* info;
+  unsigned long long cap;       // records per bucket
+  unsigned long long ocap;      // overflow records
+  unsigned long long* fill;     // [P + 1]
+};
+
+cudaError_t launch_part_scatter(const PartGeom& g, const PartWindows& w, const PartRecords& r,
+                                cudaStream_t stream, int num_sms);
+cudaError_t launch_part_pass(const PartGeom& g, const PartRecords& r, unsigned mode,
+                             cudaStream_t stream, int num_sms);
+
 struct LaunchShape {
   int block_threads;
   int windows_per_thread;
@@ -145,7 +194,8 @@ cudaError_t launch_pass(const PassBatch& b, const LaunchShape& shape, bool warp_
                         cudaStream_t stream);
 cudaError_t launch_classify(const ClassBatch& b, cudaStream_t stream, int num_sms);
 cudaError_t launch_table_init(Slot* table, unsigned long long slots, cudaStream_t stream);
-cudaError_t launch_query(const Slot* table, unsigned long long slots, unsigned int k,
+cudaError_t launch_query(const Slot* table, unsigned long long slots, unsigned int parts,
+                         unsigned int k,
                          unsigned int canonical, unsigned int min_depth, unsigned int min_ext,
                          const unsigned long long* keys, unsigned long long n,
                          unsigned int* counts, unsigned int* ext, unsigned char* codes,

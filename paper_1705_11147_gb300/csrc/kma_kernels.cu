@@ -22,202 +22,9 @@
 // k-mer reached the table through another occurrence. Every occurrence of every k-mer with
 // two or more occurrences is therefore counted exactly once; singletons are either absent
 // or (false positives) present with count 1, which any min_depth >= 2 removes.
-#include "kma_internal.cuh"
+#include "kma_device.cuh"
 
 namespace kma {
-
-typedef unsigned long long u64;
-typedef unsigned __int128 u128;
-
-// ------------------------------------------------------------------ hashing
-
-// 64-bit finaliser of MurmurHash3 (Appleby).
-__device__ __forceinline__ u64 fmix64(u64 x) {
-  x ^= x >> 33;
-  x *= 0xff51afd7ed558ccdull;
-  x ^= x >> 33;
-  x *= 0xc4ceb9fe1a85ec53ull;
-  x ^= x >> 33;
-  return x;
-}
-
-__device__ __forceinline__ u64 key_hash(u64 lo, u64 hi) {
-  return fmix64(lo ^ fmix64(hi + 0x9e3779b97f4a7c15ull));
-}
-
-__device__ __forceinline__ u64 table_index(u64 h, u64 slots) { return __umul64hi(fmix64(h ^ 0x2545f4914f6cdd1dull), slots); }
-__device__ __forceinline__ u64 bloom_index(u64 h, u64 words) { return __umul64hi(h, words); }
-__device__ __forceinline__ unsigned owner_of(u64 h, unsigned n_parts) {
-  return (unsigned)__umul64hi(fmix64(h ^ 0x9fb21c651e98df25ull), n_parts);
-}
-
-__device__ __forceinline__ u64 bloom_mask(u64 h, unsigned nbits) {
-  u64 g = fmix64(h + 0x632be59bd9b4e019ull);
-  u64 m = 0;
-  for (unsigned i = 0; i < nbits; ++i) m |= 1ull << ((g >> (6 * i)) & 63);
-  return m;
-}
-
-// ------------------------------------------------------------------ 2-bit words
-
-// Reverse the order of the 32 two-bit groups of x.
-__device__ __forceinline__ u64 rev2(u64 x) {
-  x = __brevll(x);
-  return ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
-}
-
-// Reverse complement of a k-mer held in the low 2k bits of (hi:lo).
-__device__ __forceinline__ void revcomp(u64 lo, u64 hi, unsigned k, u64& rlo, u64& rhi) {
-  u128 r = ((u128)rev2(lo) << 64) | (u128)rev2(hi);
-  r = ~r;
-  r >>= (128 - 2 * k);
-  rlo = (u64)r;
-  rhi = (u64)(r >> 64);
-}
-
-__device__ __forceinline__ unsigned code_at(const u64* codes, u64 p) {
-  return (unsigned)(codes[p >> 5] >> (62 - 2 * (p & 31))) & 3u;
-}
-
-__device__ __forceinline__ unsigned bit_at(const u64* bits, u64 p) {
-  return (unsigned)(bits[p >> 6] >> (63 - (p & 63))) & 1u;
-}
-
-struct Window {
-  u64 lo, hi;        // canonical key
-  unsigned lb, rb;   // extension bases in the key's orientation
-  bool lu, ru;       // usable (exists, A/C/G/T, Phred >= threshold)
-};
-
-// Window starting at arena position q: returns false if any of its k positions is invalid.
-__device__ __forceinline__ bool load_window(const PassDesc& D, u64 q, Window& w) {
-  const unsigned k = D.k;
-  const u64 v = q >> 6;
-  const unsigned t = (unsigned)(q & 63);
-  u64 x = D.inv[v] << t;
-  if (t) x |= D.inv[v + 1] >> (64 - t);
-  if (x >> (64 - k)) return false;
-
-  const u64 wi = q >> 5;
-  const unsigned s = 2 * (unsigned)(q & 31);
-  const u64 a = D.codes[wi], b = D.codes[wi + 1], c = D.codes[wi + 2];
-  u128 top = ((u128)a << 64) | (u128)b;
-  if (s) top = (top << s) | (u128)(c >> (64 - s));
-  const u128 fw = top >> (128 - 2 * k);
-  const u64 flo = (u64)fw, fhi = (u64)(fw >> 64);
-
-  // Extension bases: position q-1 (before) and q+k (after).
-  const bool bu = q > 0 && bit_at(D.hq, q - 1);
-  const bool au = bit_at(D.hq, q + k) != 0;
-  const unsigned bb = q > 0 ? code_at(D.codes, q - 1) : 0u;
-  const unsigned ab = (unsigned)(top >> (126 - 2 * k)) & 3u;  // the base right after the window
-
-  u64 rlo, rhi;
-  revcomp(flo, fhi, k, rlo, rhi);
-  const bool forward = !D.canonical || (fhi < rhi) || (fhi == rhi && flo <= rlo);
-  if (forward) {
-    w.lo = flo; w.hi = fhi;
-    w.lb = bb; w.lu = bu;
-    w.rb = ab; w.ru = au;
-  } else {
-    w.lo = rlo; w.hi = rhi;
-    w.lb = 3u - ab; w.lu = au;
-    w.rb = 3u - bb; w.ru = bu;
-  }
-  return true;
-}
-
-// ------------------------------------------------------------------ table
-
-__device__ __forceinline__ void cas128(Slot* s, u64 cmp_lo, u64 cmp_hi, u64 new_lo, u64 new_hi,
-                                       u64& old_lo, u64& old_hi) {
-  asm volatile(
-      "{\n\t"
-      ".reg .b128 d, c, n;\n\t"
-      "mov.b128 c, {%2, %3};\n\t"
-      "mov.b128 n, {%4, %5};\n\t"
-      "atom.global.cas.b128 d, [%6], c, n;\n\t"
-      "mov.b128 {%0, %1}, d;\n\t"
-      "}"
-      : "=l"(old_lo), "=l"(old_hi)
-      : "l"(cmp_lo), "l"(cmp_hi), "l"(new_lo), "l"(new_hi), "l"(s)
-      : "memory");
-}
-
-// Insert-if-absent. Keys are written once (empty -> key) by a 16-byte CAS and never change
-// again. A plain 16-byte load may observe a half-written slot; any value with a word still
-// equal to the empty pattern is therefore resolved by the CAS itself, which is atomic.
-// Returns the slot or nullptr (probe limit reached: the table is full).
-__device__ __forceinline__ Slot* find_or_insert(Slot* table, u64 slots, u64 lo, u64 hi, u64 h,
-                                                bool& inserted) {
-  u64 idx = table_index(h, slots);
-  const u64 limit = slots < kMaxProbe ? slots : kMaxProbe;
-  inserted = false;
-  for (u64 n = 0; n < limit; ++n) {
-    Slot* s = table + idx;
-    const ulonglong2 kv = __ldcg(reinterpret_cast<const ulonglong2*>(s));
-    if (kv.x == lo && kv.y == hi) return s;
-    if (kv.y == kEmpty || kv.x == kEmpty) {
-      u64 olo, ohi;
-      cas128(s, kEmpty, kEmpty, lo, hi, olo, ohi);
-      if (olo == kEmpty && ohi == kEmpty) { inserted = true; return s; }
-      if (olo == lo && ohi == hi) return s;
-    }
-    idx = (idx + 1 == slots) ? 0 : idx + 1;
-  }
-  return nullptr;
-}
-
-// Lookup in a table no thread is modifying. nullptr if absent; sets `full` if the probe
-// limit was reached without finding an empty slot.
-__device__ __forceinline__ const Slot* find(const Slot* table, u64 slots, u64 lo, u64 hi, u64 h,
-                                            bool& full) {
-  u64 idx = table_index(h, slots);
-  const u64 limit = slots < kMaxProbe ? slots : kMaxProbe;
-  full = false;
-  for (u64 n = 0; n < limit; ++n) {
-    const Slot* s = table + idx;
-    const ulonglong2 kv = __ldcg(reinterpret_cast<const ulonglong2*>(s));
-    if (kv.x == lo && kv.y == hi) return s;
-    if (kv.y == kEmpty) return nullptr;
-    idx = (idx + 1 == slots) ? 0 : idx + 1;
-  }
-  full = true;
-  return nullptr;
-}
-
-__device__ __forceinline__ void add_occurrence(Slot* s, const Window& w, unsigned inc,
-                                               DevStatus* st) {
-  const unsigned old = atomicAdd(&s->count, inc);
-  if (old > 0xFFFFFFFFu - inc) atomicOr(&st->flags, kFlagOverflow);
-  if (w.lu) atomicAdd(&s->ext[w.lb], 1u);
-  if (w.ru) atomicAdd(&s->ext[4 + w.rb], 1u);
-}
-
-// Warp-aggregated variant: lanes in `act` holding the same slot merge their count into one
-// atomic, and lanes adding to the same extension counter merge theirs.
-__device__ __forceinline__ void add_occurrence_agg(unsigned act, Slot* s, const Window& w,
-                                                   DevStatus* st) {
-  const int lane = threadIdx.x & 31;
-  const unsigned peers = __match_any_sync(act, reinterpret_cast<u64>(s));
-  if (lane == __ffs(peers) - 1) {
-    const unsigned inc = __popc(peers);
-    const unsigned old = atomicAdd(&s->count, inc);
-    if (old > 0xFFFFFFFFu - inc) atomicOr(&st->flags, kFlagOverflow);
-  }
-  const unsigned lact = __ballot_sync(act, w.lu);
-  if (w.lu) {
-    unsigned* a = &s->ext[w.lb];
-    const unsigned m = __match_any_sync(lact, reinterpret_cast<u64>(a));
-    if (lane == __ffs(m) - 1) atomicAdd(a, (unsigned)__popc(m));
-  }
-  const unsigned ract = __ballot_sync(act, w.ru);
-  if (w.ru) {
-    unsigned* a = &s->ext[4 + w.rb];
-    const unsigned m = __match_any_sync(ract, reinterpret_cast<u64>(a));
-    if (lane == __ffs(m) - 1) atomicAdd(a, (unsigned)__popc(m));
-  }
-}
 
 // ------------------------------------------------------------------ pass kernel
 
@@ -228,46 +35,6 @@ __device__ __forceinline__ int find_pass_sample(const PassBatch& B, u64 t) {
     if (B.d[mid].tile_begin <= t) lo = mid; else hi = mid;
   }
   return lo;
-}
-
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-// Insert-if-absent continuing from a first probe whose slot (index idx) is already loaded.
-__device__ __forceinline__ Slot* resolve_insert(Slot* table, u64 slots, u64 idx, ulonglong2 kv,
-                                                u64 lo, u64 hi, bool& inserted) {
-  const u64 limit = slots < kMaxProbe ? slots : kMaxProbe;
-  inserted = false;
-  for (u64 n = 0; n < limit; ++n) {
-    Slot* s = table + idx;
-    if (n) kv = __ldcg(reinterpret_cast<const ulonglong2*>(s));
-    if (kv.x == lo && kv.y == hi) return s;
-    if (kv.y == kEmpty || kv.x == kEmpty) {
-      u64 olo, ohi;
-      cas128(s, kEmpty, kEmpty, lo, hi, olo, ohi);
-      if (olo == kEmpty && ohi == kEmpty) { inserted = true; return s; }
-      if (olo == lo && ohi == hi) return s;
-    }
-    idx = (idx + 1 == slots) ? 0 : idx + 1;
-  }
-  return nullptr;
-}
-
-// Lookup (table not being modified) continuing from a loaded first probe.
-__device__ __forceinline__ Slot* resolve_find(Slot* table, u64 slots, u64 idx, ulonglong2 kv,
-                                              u64 lo, u64 hi, bool& full) {
-  const u64 limit = slots < kMaxProbe ? slots : kMaxProbe;
-  full = false;
-  for (u64 n = 0; n < limit; ++n) {
-    Slot* s = table + idx;
-    if (n) kv = __ldcg(reinterpret_cast<const ulonglong2*>(s));
-    if (kv.x == lo && kv.y == hi) return s;
-    if (kv.y == kEmpty) return nullptr;
-    idx = (idx + 1 == slots) ? 0 : idx + 1;
-  }
-  full = true;
-  return nullptr;
 }
 
 // One tile = blockDim.x * WPT consecutive window starts; thread t takes starts
@@ -583,14 +350,6 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
 
 // ------------------------------------------------------------------ classify + compact
 
-__device__ __forceinline__ unsigned side_code(const unsigned* e, unsigned min_ext) {
-  unsigned n = 0, b = 0;
-#pragma unroll
-  for (unsigned j = 0; j < 4; ++j)
-    if (e[j] >= min_ext) { ++n; b = j; }
-  return n == 0 ? 4u : (n >= 2 ? 5u : b);
-}
-
 __device__ __forceinline__ int find_class_sample(const ClassBatch& B, u64 blk) {
   int lo = 0, hi = (int)B.n;
   while (hi - lo > 1) {
@@ -683,7 +442,9 @@ __global__ void __launch_bounds__(kClassThreads) classify_kernel(const __grid_co
 
 // ------------------------------------------------------------------ query
 
-__global__ void __launch_bounds__(256) query_kernel(const Slot* table, u64 slots, unsigned k,
+// slots = slots per partition, parts = on-chip partitions (1: one table).
+__global__ void __launch_bounds__(256) query_kernel(const Slot* table, u64 slots, unsigned parts,
+                                                    unsigned k,
                                                     unsigned canonical, unsigned min_depth,
                                                     unsigned min_ext, const u64* keys, u64 n,
                                                     unsigned* counts, unsigned* ext,
@@ -702,7 +463,9 @@ __global__ void __launch_bounds__(256) query_kernel(const Slot* table, u64 slots
       const bool forward = !canonical || (qhi < rhi) || (qhi == rhi && qlo <= rlo);
       const u64 lo = forward ? qlo : rlo, hi = forward ? qhi : rhi;
       bool full;
-      const Slot* s = find(table, slots, lo, hi, key_hash(lo, hi), full);
+      const u64 h = key_hash(lo, hi);
+      const Slot* sub = parts > 1 ? table + (u64)part_of(h, parts) * slots : table;
+      const Slot* s = find(sub, slots, lo, hi, h, full);
       if (full) atomicOr(&st->flags, kFlagFull);
       if (s && s->count >= min_depth) {
         c = s->count;
@@ -807,14 +570,14 @@ cudaError_t launch_table_init(Slot* table, u64 slots, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_query(const Slot* table, u64 slots, unsigned k, unsigned canonical,
+cudaError_t launch_query(const Slot* table, u64 slots, unsigned parts, unsigned k, unsigned canonical,
                          unsigned min_depth, unsigned min_ext, const u64* keys, u64 n,
                          unsigned* counts, unsigned* ext, unsigned char* codes, DevStatus* st,
                          cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   u64 blocks = (n + 255) / 256;
   if (blocks > 152ull * 16) blocks = 152ull * 16;
-  query_kernel<<<(unsigned)blocks, 256, 0, stream>>>(table, slots, k, canonical, min_depth, min_ext,
+  query_kernel<<<(unsigned)blocks, 256, 0, stream>>>(table, slots, parts, k, canonical, min_depth, min_ext,
                                                      keys, n, counts, ext, codes, st);
   return cudaGetLastError();
 }

@@ -140,6 +140,22 @@ def test_table_and_arena_sizing(lib):
     assert nb.bloom_words == 0
 
 
+def test_partition_sizing(lib):
+    from paper_1705_11147_gb300 import capi
+    small = _plan(k=51, max_bases=30_000_000, expected_distinct=4_400_000, expected_keys=1_100_000)
+    assert small.partitions == 1                      # filter + table below 256 MB: one table
+    big = _plan(k=51, max_bases=6_000_000_000, expected_distinct=2_100_000_000,
+                expected_keys=300_000_000)
+    per_part = (big.bloom_words * 8 + big.table_slots * 64) / big.partitions
+    assert big.partitions > 1 and per_part <= 48 * 2**20 * 1.01
+    assert big.bloom_words % big.partitions == 0 and big.table_slots % big.partitions == 0
+    forced = _plan(k=31, max_bases=1_000_000, partitions=7)
+    assert forced.partitions == 7 and forced.table_slots % 7 == 0
+    one = _plan(k=31, max_bases=6_000_000_000, expected_distinct=2_100_000_000, partitions=1)
+    assert one.partitions == 1
+    assert _plan_rc(k=31, max_bases=1000, partitions=5000) == capi.KMA_EINVAL
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_1705_11147_gb300 import capi
     saved = capi._LIB

@@ -129,6 +129,10 @@ def test_low_complexity_and_repeats(gpu):
             for bloom in (False, True):
                 assert_same(run_gpu(gpu, rs, warp_aggregate=agg, use_bloom=bloom), want,
                             f"k={k} agg={agg} bloom={bloom}")
+        # partitioned: the repeated k-mers overfill their buckets and spill into the
+        # overflow area
+        for bloom in (False, True):
+            assert_same(run_gpu(gpu, rs, partitions=5, use_bloom=bloom), want, f"k={k} partitioned")
 
 
 def test_edge_inputs(gpu):
@@ -189,6 +193,33 @@ def test_multiple_count_calls(gpu, plain):
 def test_results_independent_of_tuning(gpu, plain, shape):
     rs, want = plain
     assert_same(run_gpu(gpu, rs, **shape), want, str(shape))
+
+
+@pytest.mark.parametrize("opts", [
+    dict(partitions=7),
+    dict(partitions=64, windows_per_thread=1),
+    dict(partitions=4096),                      # many tiny partitions
+    dict(partitions=5, use_bloom=False, min_depth=2),
+    dict(partitions=3, expected_distinct=50_000, bloom_fpr=0.3, table_capacity=9_000_000),
+])
+def test_partitioned_mode(gpu, plain, opts):
+    """On-chip owner-computes partitions give the same records as one table."""
+    rs, want = plain
+    got = run_gpu(gpu, rs, **opts)
+    assert_same(got, want, str(opts))
+    assert got.valid_windows == want.valid_windows
+
+
+def test_partitioned_batches_host_inputs_and_k63(gpu, plain):
+    rs, want = plain
+    assert_same(run_gpu(gpu, rs, partitions=16, batches=4), want, "4 count() calls")
+    assert_same(run_gpu(gpu, rs, partitions=16, device_inputs=False, staging_bytes=4 << 20), want, "host")
+    rr = synth.random_reads(seed=1234, n_reads=4000, min_len=50, max_len=200,
+                            alphabet=b"ACGTACGTACGTacgtN", q_lo=10, q_hi=30)
+    rr.seq[: rr.n_bases // 3] = np.frombuffer((b"ACGTTGCAGG" * (rr.n_bases // 30 + 1))[: rr.n_bases // 3], np.uint8)
+    for k in (63, 21):
+        rr.meta["params"] = dict(k=k, min_depth=2, min_ext_count=1, qual_threshold=20)
+        assert_same(run_gpu(gpu, rr, partitions=9), oracle_for(rr), f"k={k} partitioned")
 
 
 def test_bacterial_5m_full(gpu):
@@ -258,22 +289,24 @@ def test_query_matches_oracle(gpu):
     singles = low.keys[low.counts == 1][:500]
     q = np.concatenate([present, rc, rand, singles])
     p = rs.meta["params"]
-    with KmerAnalysis(make_params(k=51, max_bases=rs.n_bases, max_reads=rs.n_reads,
-                                  expected_distinct=rs.n_bases, min_depth=p["min_depth"])) as ka:
-        seq, qual, offs = to_dev(gpu, rs)
-        ka.count(seq, qual, offs)
-        ka.finalize()
-        c, e, cd = ka.query(q)
-        qd = gpu.from_numpy(q.astype(np.int64)).cuda()
-        c2, e2, cd2 = ka.query(qd)
-        gpu.cuda.synchronize()
     wc, we, wcd = want.query(q)
-    np.testing.assert_array_equal(c, wc)
-    np.testing.assert_array_equal(e, we)
-    np.testing.assert_array_equal(cd, wcd)
-    np.testing.assert_array_equal(c2.cpu().numpy().astype(np.uint32), wc)
-    np.testing.assert_array_equal(e2.cpu().numpy().astype(np.uint32), we)
-    assert (c[:3000] > 0).all() and (c[len(present) + 1500 + 1000:] == 0).all()
+    for parts in (1, 11):
+        with KmerAnalysis(make_params(k=51, max_bases=rs.n_bases, max_reads=rs.n_reads,
+                                      expected_distinct=rs.n_bases, min_depth=p["min_depth"],
+                                      partitions=parts)) as ka:
+            seq, qual, offs = to_dev(gpu, rs)
+            ka.count(seq, qual, offs)
+            ka.finalize()
+            c, e, cd = ka.query(q)
+            qd = gpu.from_numpy(q.astype(np.int64)).cuda()
+            c2, e2, cd2 = ka.query(qd)
+            gpu.cuda.synchronize()
+        np.testing.assert_array_equal(c, wc)
+        np.testing.assert_array_equal(e, we)
+        np.testing.assert_array_equal(cd, wcd)
+        np.testing.assert_array_equal(c2.cpu().numpy().astype(np.uint32), wc)
+        np.testing.assert_array_equal(e2.cpu().numpy().astype(np.uint32), we)
+        assert (c[:3000] > 0).all() and (c[len(present) + 1500 + 1000:] == 0).all()
 
 
 def test_count_batch_equals_solo_and_oracle(gpu):
@@ -281,10 +314,11 @@ def test_count_batch_equals_solo_and_oracle(gpu):
     specs = synth.batched_specs(6, scale=0.02)
     sets = [synth.sample_reads(s) for s in specs]
     handles, reads = [], []
-    for rs in sets:
+    for i, rs in enumerate(sets):
         p = rs.meta["params"]
         handles.append(KmerAnalysis(make_params(k=p["k"], min_depth=p["min_depth"], max_bases=rs.n_bases,
-                                                max_reads=rs.n_reads, expected_distinct=rs.n_bases)))
+                                                max_reads=rs.n_reads, expected_distinct=rs.n_bases,
+                                                partitions=5 if i % 3 == 1 else 1)))
         reads.append(to_dev(gpu, rs))
     count_batch(handles, reads)
     finalize_batch(handles)
