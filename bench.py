@@ -406,6 +406,150 @@ def run_e2e(args, ka, rs, dev, qkeys_dev, ws):
             "ms_per_step": round(dt * 1e3, 2)}
 
 
+# ------------------------------------------------------------------ batched (many samples)
+
+def run_batched(args, ws, rank, local):
+    """64 independent samples of uneven size: one captured CUDA graph per step (reset, one
+    packing and one persistent counting launch for all samples, one recount and one
+    classification launch), against the plain path that runs create -> count -> finalize ->
+    destroy for one sample after another on the same device-resident reads."""
+    import torch
+    from paper_1705_11147_gb300 import BatchGraph, KmerAnalysis
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t_gen = time.perf_counter()
+    specs = synth.batched_specs(args.samples, scale=args.scale)
+    sets = [synth.sample_reads(sp) for sp in specs]
+    t_gen = time.perf_counter() - t_gen
+    reads = [(torch.from_numpy(rs.seq).to(dev), torch.from_numpy(rs.qual).to(dev),
+              torch.from_numpy(rs.offsets.astype(np.int64)).to(dev)) for rs in sets]
+
+    def params(rs):
+        return make_handle_params(rs, partitions=1, **args.tuning)
+
+    handles = [KmerAnalysis(params(rs)) for rs in sets]
+    g = BatchGraph(handles, reads)
+    for _ in range(args.warmup):
+        g.replay()
+    g.stream.synchronize()
+    for h in handles:
+        h.timings(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0.record(g.stream)
+    for _ in range(args.steps):
+        g.replay()
+    ev1.record(g.stream)
+    g.stream.synchronize()
+    clk = clocks.stop()
+    ms_batched = ev0.elapsed_time(ev1) / args.steps
+    infos = g.results()
+    windows = sum(int(r.valid_windows) for r in infos)
+    launches = g.kernels_per_replay
+    for h in handles:
+        h.destroy()
+    del g
+
+    # plain: one job per launch sequence, sample after sample
+    stream = torch.cuda.current_stream(dev)
+
+    def plain_once():
+        n = 0
+        for rs, (sq, ql, of) in zip(sets, reads):
+            with KmerAnalysis(params(rs), stream=stream) as ka:
+                ka.count(sq, ql, of)
+                n += int(ka.finalize().valid_windows)
+        return n
+
+    plain_once()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    reps = max(1, min(args.steps, 3))
+    for _ in range(reps):
+        wp = plain_once()
+    torch.cuda.synchronize(dev)
+    ms_plain = (time.perf_counter() - t0) * 1e3 / reps
+    assert wp == windows
+    value = windows / (ms_batched * 1e-3) / 1e9
+    plain_value = windows / (ms_plain * 1e-3) / 1e9
+    return {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_batched, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "batched_64", "samples": len(sets),
+                       "bases": int(sum(rs.n_bases for rs in sets)), "valid_windows": windows,
+                       "k": 51, "scale": args.scale, "mode": "one CUDA graph per step"},
+            "plain": {"value": round(plain_value, 3), "unit": UNIT, "ms_per_step": round(ms_plain, 2),
+                      "path": "create -> count -> finalize -> destroy per sample"},
+            "batched_vs_plain": round(value / plain_value, 3), "gpu_launches": int(launches),
+            "clocks": clk, "generation_s": round(t_gen, 1)}
+
+
+# ------------------------------------------------------------------ served (job stream)
+
+def run_served(args, ws, rank, local):
+    """Counting jobs (genome log-U[1, 50] Mbp x scale, 30x of 150 bp, k in {31, 51}) through the
+    continuous-batching server: saturation throughput with every job released at once against
+    the plain one-job-at-a-time path, then p50/p99 latency with Poisson arrivals."""
+    import torch
+    from paper_1705_11147_gb300.serve import Job, Server, run_plain
+    torch.cuda.set_device(local)
+    t_gen = time.perf_counter()
+    specs = synth.served_specs(args.jobs, scale=args.scale)
+    jobs = []
+    for i, sp in enumerate(specs):
+        rs = synth.sample_reads(sp)
+        p = dict(rs.meta["params"])
+        p.pop("bloom_fpr", None)
+        p.update(workload_sizing(rs))
+        jobs.append(Job(rs.seq, rs.qual, rs.offsets, params=p, job_id=i,
+                        meta={"arrival_s": sp["arrival_s"], "windows": rs.windows_upper_bound(p["k"])}))
+    t_gen = time.perf_counter() - t_gen
+
+    def saturate():
+        with Server(max_batch=args.max_batch, workers=args.workers) as srv:
+            t0 = time.perf_counter()
+            futs = [srv.submit(j) for j in jobs]
+            res = [f.result() for f in futs]
+            dt = time.perf_counter() - t0
+        return dt, res, srv.batches
+
+    saturate()  # warm-up (pools, module load)
+    t_srv, res_srv, batches = saturate()
+    t0 = time.perf_counter()
+    res_plain = run_plain(jobs)
+    t_plain = time.perf_counter() - t0
+    windows = sum(int(r.valid_windows) for r in res_srv)
+    same = all(len(a) == len(b) for a, b in zip(res_srv, res_plain))
+    # latency under Poisson arrivals (arrival times of the first jobs, in real time)
+    n_lat = min(len(jobs), args.latency_jobs)
+    with Server(max_batch=args.max_batch, workers=args.workers) as srv:
+        start = time.perf_counter()
+        futs = []
+        for j in jobs[:n_lat]:
+            delay = j.meta["arrival_s"] - (time.perf_counter() - start)
+            if delay > 0:
+                time.sleep(delay)
+            futs.append(srv.submit(j))
+        for f in futs:
+            f.result()
+        lat = srv.latency_stats()
+    value = windows / t_srv / 1e9
+    plain_value = windows / t_plain / 1e9
+    return {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": 1,
+            "warmup": 1, "ms_per_step": round(t_srv * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "served_500", "jobs": len(jobs), "scale": args.scale,
+                       "bases": int(sum(j.n_bases for j in jobs)), "valid_windows": windows,
+                       "max_batch": args.max_batch, "workers": args.workers,
+                       "saturation": "all jobs released at t=0"},
+            "plain": {"value": round(plain_value, 3), "unit": UNIT, "seconds": round(t_plain, 3),
+                      "path": "create -> count (host reads) -> finalize -> copy -> destroy, one job at a time"},
+            "served_vs_plain": round(value / plain_value, 3), "batches": batches,
+            "records_match_plain": bool(same),
+            "latency": {"jobs": n_lat, "rate_per_s": 4.0, **lat}, "generation_s": round(t_gen, 1)}
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, ws, rank):
@@ -449,7 +593,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large_200m", choices=list(synth.WORKLOADS))
+    ap.add_argument("--workload", default="large_200m",
+                    choices=list(synth.WORKLOADS) + ["batched_64", "served_500"])
+    ap.add_argument("--samples", type=int, default=64)
+    ap.add_argument("--jobs", type=int, default=500)
+    ap.add_argument("--latency-jobs", type=int, default=60)
+    ap.add_argument("--max-batch", type=int, default=16)
+    ap.add_argument("--workers", type=int, default=3)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--queries", type=int, default=1_000_000)
     ap.add_argument("--no-e2e", action="store_true")
@@ -470,7 +620,12 @@ def main():
     else:
         from paper_1705_11147_gb300 import build
         build.build()
-        out = run_ours(args, ws, rank, local)
+        if args.workload == "batched_64":
+            out = run_batched(args, ws, rank, local)
+        elif args.workload == "served_500":
+            out = run_served(args, ws, rank, local)
+        else:
+            out = run_ours(args, ws, rank, local)
     if out is not None and rank == 0:
         print(json.dumps(out), flush=True)
 

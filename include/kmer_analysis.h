@@ -239,6 +239,18 @@ int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uin
  * handle's code is returned and the others are still finalized. */
 int kmer_analysis_finalize_batch(kma_handle* const* hs, uint32_t n, kma_result* out);
 
+/* ---- Capture-safe finalize (for CUDA graphs of whole batched steps) -------------------
+ * kmer_analysis_reserve_output allocates result buffers for up to n_records records now, so
+ * that kmer_analysis_finalize_batch_async needs no allocation: it enqueues the recount and
+ * classification of n handles on hs[0]'s stream without any host synchronisation and marks
+ * them finalized (it can be captured into a CUDA graph together with kmer_analysis_reset and
+ * kmer_analysis_count_batch). kmer_analysis_fetch_result then synchronises the handle's
+ * stream and reads the result of the last completed finalize (*out->n may exceed the
+ * reserved capacity: KMA_EFULL, reserve more and run again). */
+int kmer_analysis_reserve_output(kma_handle* h, uint64_t n_records);
+int kmer_analysis_finalize_batch_async(kma_handle* const* hs, uint32_t n);
+int kmer_analysis_fetch_result(kma_handle* h, kma_result* out);
+
 /* ---- Allocation-free counting for small read sets --------------------------------------
  * The paper has no counterpart: this entry point serves callers that must not allocate
  * device memory when they count, for example code that reserves a fixed memory budget at

@@ -80,6 +80,9 @@ _SIGS = {
     "kmer_analysis_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "kmer_analysis_count_batch": ([ctypes.POINTER(vp), ctypes.POINTER(kma_reads), u32], ctypes.c_int),
     "kmer_analysis_finalize_batch": ([ctypes.POINTER(vp), u32, ctypes.POINTER(kma_result)], ctypes.c_int),
+    "kmer_analysis_reserve_output": ([vp, u64], ctypes.c_int),
+    "kmer_analysis_finalize_batch_async": ([ctypes.POINTER(vp), u32], ctypes.c_int),
+    "kmer_analysis_fetch_result": ([vp, ctypes.POINTER(kma_result)], ctypes.c_int),
     "kmer_analysis_count_small_noalloc": ([ctypes.POINTER(kma_params), vp, vp, vp, u64, u64, vp, vp,
                                            vp, vp, u64, ctypes.POINTER(u64), vp], ctypes.c_int),
 }

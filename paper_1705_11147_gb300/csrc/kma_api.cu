@@ -675,26 +675,10 @@ int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual, const 
   return KMA_OK;
 }
 
-static int finalize_many(kma_handle* const* hs, uint32_t n, kma_result* out) {
-  if (!hs || n == 0 || n > KMA_MAX_BATCH) return KMA_EINVAL;
+// Recount pass (first sightings) of the Bloom handles: one launch for all one-table handles,
+// one per record batch of the partitioned ones. Enqueued on h0's stream.
+static int enqueue_recount(kma_handle* const* hs, uint32_t n) {
   kma_handle* h0 = hs[0];
-  for (uint32_t i = 0; i < n; ++i) {
-    if (!hs[i]) return KMA_EINVAL;
-    if (hs[i]->finalized || hs[i]->failed) return KMA_ESTATE;
-  }
-  // make every handle's stream work visible to h0's stream
-  std::vector<cudaEvent_t> evs;
-  for (uint32_t i = 1; i < n; ++i) {
-    if (hs[i]->stream != h0->stream) {
-      cudaEvent_t ev;
-      KMA_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-      KMA_CUDA(cudaEventRecord(ev, hs[i]->stream));
-      KMA_CUDA(cudaStreamWaitEvent(h0->stream, ev, 0));
-      evs.push_back(ev);
-    }
-  }
-  for (auto ev : evs) cudaEventDestroy(ev);
-  // 1. recount pass over the Bloom handles
   PassBatch pb;
   std::memset(&pb, 0, sizeof(pb));
   pb.prefetch = h0->prefetch;
@@ -709,11 +693,9 @@ static int finalize_many(kma_handle* const* hs, uint32_t n, kma_result* out) {
     pb.d[pb.n++] = d;
   }
   pb.total_tiles = tiles;
-  {
-    int rc = timed_launch(h0, KMA_KERNEL_RECOUNT, h0->stream, pb.n > 0 && tiles > 0,
-                          [&] { return launch_pass(pb, h0->shape, h0->agg, h0->stream); });
-    if (rc) return rc;
-  }
+  int rc = timed_launch(h0, KMA_KERNEL_RECOUNT, h0->stream, pb.n > 0 && tiles > 0,
+                        [&] { return launch_pass(pb, h0->shape, h0->agg, h0->stream); });
+  if (rc) return rc;
   for (uint32_t i = 0; i < n; ++i) {  // partitioned handles: recount their record buckets
     kma_handle* h = hs[i];
     if (!h->p.use_bloom || h->d.P <= 1) continue;
@@ -721,32 +703,20 @@ static int finalize_many(kma_handle* const* hs, uint32_t n, kma_result* out) {
     for (auto& rb : h->rec_batches) {
       PartRecords r;
       r.keys = rb.keys; r.info = rb.info; r.cap = rb.cap; r.ocap = rb.ocap; r.fill = rb.fill;
-      int rc = timed_launch(h0, KMA_KERNEL_RECOUNT, h0->stream, true,
-                            [&] { return launch_part_pass(g, r, kModeRecount, h0->stream, h0->num_sms); });
+      rc = timed_launch(h0, KMA_KERNEL_RECOUNT, h0->stream, true,
+                        [&] { return launch_part_pass(g, r, kModeRecount, h0->stream, h0->num_sms); });
       if (rc) return rc;
     }
   }
-  // 2. statuses -> output capacities
-  for (uint32_t i = 0; i < n; ++i) {
-    kma_handle* h = hs[i];
-    KMA_CUDA(cudaMemsetAsync(&h->status->n_out, 0, 2 * sizeof(u64), h0->stream));
-    KMA_CUDA(cudaMemcpyAsync(h->host_status, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, h0->stream));
-  }
-  KMA_CUDA(cudaStreamSynchronize(h0->stream));
-  int first_err = KMA_OK;
-  std::vector<int> ok(n, 0);
-  for (uint32_t i = 0; i < n; ++i) {
-    kma_handle* h = hs[i];
-    int rc = flags_to_code(h->host_status->flags);
-    if (rc) { h->failed = true; if (!first_err) first_err = rc; continue; }
-    cudaStream_t saved = h->stream;
-    h->stream = h0->stream;
-    rc = ensure_output(h, h->host_status->table_keys);
-    h->stream = saved;
-    if (rc) { h->failed = true; if (!first_err) first_err = rc; continue; }
-    ok[i] = 1;
-  }
-  // 3. classify + compact
+  return KMA_OK;
+}
+
+// Classification + compaction of the handles with ok[i] into their current output buffers,
+// one launch; then their record buckets are released. Enqueued on h0's stream.
+static int enqueue_classify(kma_handle* const* hs, uint32_t n, const std::vector<int>& ok) {
+  kma_handle* h0 = hs[0];
+  for (uint32_t i = 0; i < n; ++i)
+    if (ok[i]) KMA_CUDA(cudaMemsetAsync(&hs[i]->status->n_out, 0, 2 * sizeof(u64), h0->stream));
   ClassBatch cb;
   std::memset(&cb, 0, sizeof(cb));
   cb.write = 1;
@@ -759,25 +729,71 @@ static int finalize_many(kma_handle* const* hs, uint32_t n, kma_result* out) {
     cb.d[cb.n++] = c;
   }
   cb.total_blocks = blocks;
-  {
-    int rc = timed_launch(h0, KMA_KERNEL_CLASSIFY, h0->stream, cb.n > 0 && blocks > 0,
-                          [&] { return launch_classify(cb, h0->stream, h0->num_sms); });
-    if (rc) return rc;
-  }
-  for (uint32_t i = 0; i < n; ++i) {
-    if (ok[i]) KMA_CUDA(cudaMemcpyAsync(hs[i]->host_status, hs[i]->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, h0->stream));
-    // the record buckets are not needed after the recount
+  int rc = timed_launch(h0, KMA_KERNEL_CLASSIFY, h0->stream, cb.n > 0 && blocks > 0,
+                        [&] { return launch_classify(cb, h0->stream, h0->num_sms); });
+  if (rc) return rc;
+  for (uint32_t i = 0; i < n; ++i) {  // the record buckets are not needed after the recount
     cudaStream_t saved = hs[i]->stream;
     hs[i]->stream = h0->stream;
     free_records(hs[i]);
     hs[i]->stream = saved;
   }
+  return KMA_OK;
+}
+
+static int check_batch(kma_handle* const* hs, uint32_t n) {
+  if (!hs || n == 0 || n > KMA_MAX_BATCH) return KMA_EINVAL;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!hs[i]) return KMA_EINVAL;
+    if (hs[i]->finalized || hs[i]->failed) return KMA_ESTATE;
+    for (uint32_t j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return KMA_EINVAL;
+  }
+  return KMA_OK;
+}
+
+static int finalize_many(kma_handle* const* hs, uint32_t n, kma_result* out) {
+  int rc = check_batch(hs, n);
+  if (rc) return rc;
+  kma_handle* h0 = hs[0];
+  // make every handle's stream work visible to h0's stream
+  for (uint32_t i = 1; i < n; ++i) {
+    if (hs[i]->stream != h0->stream) {
+      cudaEvent_t ev;
+      KMA_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      cudaError_t e = cudaEventRecord(ev, hs[i]->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h0->stream, ev, 0);
+      cudaEventDestroy(ev);
+      if (e != cudaSuccess) return cuda_fail(e, "stream ordering");
+    }
+  }
+  if ((rc = enqueue_recount(hs, n))) return rc;
+  // statuses -> output capacities (table_keys bounds the records)
+  for (uint32_t i = 0; i < n; ++i)
+    KMA_CUDA(cudaMemcpyAsync(hs[i]->host_status, hs[i]->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, h0->stream));
+  KMA_CUDA(cudaStreamSynchronize(h0->stream));
+  int first_err = KMA_OK;
+  std::vector<int> ok(n, 0);
+  for (uint32_t i = 0; i < n; ++i) {
+    kma_handle* h = hs[i];
+    int e = flags_to_code(h->host_status->flags);
+    if (e) { h->failed = true; if (!first_err) first_err = e; continue; }
+    cudaStream_t saved = h->stream;
+    h->stream = h0->stream;
+    e = ensure_output(h, h->host_status->table_keys);
+    h->stream = saved;
+    if (e) { h->failed = true; if (!first_err) first_err = e; continue; }
+    ok[i] = 1;
+  }
+  if ((rc = enqueue_classify(hs, n, ok))) return rc;
+  for (uint32_t i = 0; i < n; ++i)
+    if (ok[i]) KMA_CUDA(cudaMemcpyAsync(hs[i]->host_status, hs[i]->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, h0->stream));
   KMA_CUDA(cudaStreamSynchronize(h0->stream));
   for (uint32_t i = 0; i < n; ++i) {
     kma_handle* h = hs[i];
     if (!ok[i]) { if (out) std::memset(&out[i], 0, sizeof(kma_result)); continue; }
-    int rc = flags_to_code(h->host_status->flags);
-    if (rc) { h->failed = true; if (!first_err) first_err = rc; if (out) std::memset(&out[i], 0, sizeof(kma_result)); continue; }
+    int e = flags_to_code(h->host_status->flags);
+    if (e) { h->failed = true; if (!first_err) first_err = e; if (out) std::memset(&out[i], 0, sizeof(kma_result)); continue; }
     fill_result(h);
     h->finalized = true;
     if (out) out[i] = h->res;
@@ -793,6 +809,35 @@ int kmer_analysis_finalize(kma_handle* h, kma_result* out) {
 
 int kmer_analysis_finalize_batch(kma_handle* const* hs, uint32_t n, kma_result* out) {
   return finalize_many(hs, n, out);
+}
+
+int kmer_analysis_reserve_output(kma_handle* h, uint64_t n_records) {
+  if (!h) return KMA_EINVAL;
+  return ensure_output(h, n_records);
+}
+
+int kmer_analysis_finalize_batch_async(kma_handle* const* hs, uint32_t n) {
+  int rc = check_batch(hs, n);
+  if (rc) return rc;
+  for (uint32_t i = 0; i < n; ++i)
+    if (!hs[i]->out_keys) return KMA_ESTATE;  // kmer_analysis_reserve_output first
+  if ((rc = enqueue_recount(hs, n))) return rc;
+  std::vector<int> ok(n, 1);
+  if ((rc = enqueue_classify(hs, n, ok))) return rc;
+  for (uint32_t i = 0; i < n; ++i) hs[i]->finalized = true;
+  return KMA_OK;
+}
+
+int kmer_analysis_fetch_result(kma_handle* h, kma_result* out) {
+  if (!h) return KMA_EINVAL;
+  if (!h->finalized) return KMA_ESTATE;
+  int rc = read_status(h);
+  if (rc) return rc;
+  fill_result(h);
+  if (out) *out = h->res;
+  rc = flags_to_code(h->host_status->flags);
+  if (!rc && h->host_status->n_out > h->out_cap) rc = KMA_EFULL;
+  return rc;
 }
 
 int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uint32_t n) {

@@ -243,6 +243,71 @@ def finalize_batch(handles: list[KmerAnalysis]) -> list[capi.kma_result]:
     return list(out)
 
 
+def reserve_output(h: KmerAnalysis, n_records: int) -> None:
+    check(capi.load().kmer_analysis_reserve_output(h.handle, n_records), "reserve_output")
+
+
+def finalize_batch_async(handles: list[KmerAnalysis]) -> None:
+    """kmer_analysis_finalize_batch_async: no host synchronisation, capture-safe."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.handle.value for h in handles])
+    check(capi.load().kmer_analysis_finalize_batch_async(hs, n), "finalize_batch_async")
+
+
+def fetch_result(h: KmerAnalysis) -> capi.kma_result:
+    r = capi.kma_result()
+    check(capi.load().kmer_analysis_fetch_result(h.handle, ctypes.byref(r)), "fetch_result")
+    h.result_info = r
+    return r
+
+
+class BatchGraph:
+    """Many samples in one CUDA graph: reset -> count_batch (one packing launch and one
+    persistent counting launch for all samples) -> finalize_batch_async (one recount and one
+    classification launch), captured once and replayed. `reads[i]` = (seq, qual, offsets)
+    CUDA tensors of handle i; all handles are moved to the capture stream."""
+
+    def __init__(self, handles: list[KmerAnalysis], reads: list[tuple], headroom: float = 1.25):
+        torch = _torch()
+        assert 0 < len(handles) <= capi.KMA_MAX_BATCH and len(handles) == len(reads)
+        self.handles, self.reads = handles, reads
+        self.stream = torch.cuda.Stream()
+        for h in handles:
+            h.set_stream(self.stream)
+        # eager run: sizes the output buffers the captured finalize writes into
+        with torch.cuda.stream(self.stream):
+            self._step_eager()
+        for h in handles:
+            reserve_output(h, int(h.result_info.table_keys * headroom) + 1024)
+        before = sum(h.timings()["launches"] for h in handles)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            self._step_async()
+        self.stream.synchronize()
+        # library kernels in the graph (the host counters tick once, at capture)
+        self.kernels_per_replay = sum(h.timings()["launches"] for h in handles) - before
+
+    def _step_eager(self):
+        for h in self.handles:
+            h.reset()
+        count_batch(self.handles, self.reads)
+        finalize_batch(self.handles)
+
+    def _step_async(self):
+        for h in self.handles:
+            h.reset()
+        count_batch(self.handles, self.reads)
+        finalize_batch_async(self.handles)
+
+    def replay(self) -> None:
+        """Launch the graph on the handles' stream (results are read from that stream)."""
+        with _torch().cuda.stream(self.stream):
+            self.graph.replay()
+
+    def results(self) -> list[capi.kma_result]:
+        return [fetch_result(h) for h in self.handles]
+
+
 def count_kmers(seq, qual, offsets, k: int, min_depth: int = 2, min_ext_count: int = 2,
                 qual_threshold: int = 20, use_bloom: bool = True, canonical: bool = True,
                 expected_distinct: int = 0, expected_keys: int = 0, stream=None,

@@ -329,6 +329,27 @@ def test_count_batch_equals_solo_and_oracle(gpu):
         h.destroy()
 
 
+def test_batch_graph_replay_equals_solo(gpu):
+    """Batched samples of uneven size in one captured CUDA graph: every replay gives each
+    sample exactly its solo result."""
+    from paper_1705_11147_gb300 import BatchGraph, KmerAnalysis, make_params
+    specs = synth.batched_specs(9, scale=0.01)
+    sets = [synth.sample_reads(s) for s in specs]
+    handles = [KmerAnalysis(make_params(k=51, min_depth=2, max_bases=rs.n_bases, max_reads=rs.n_reads,
+                                        expected_distinct=rs.n_bases, partitions=1)) for rs in sets]
+    reads = [to_dev(gpu, rs) for rs in sets]
+    g = BatchGraph(handles, reads)
+    solo = [run_gpu(gpu, rs) for rs in sets]
+    for rep in range(2):
+        g.replay()
+        infos = g.results()
+        for i, h in enumerate(handles):
+            assert infos[i].n == len(solo[i])
+            assert_same(h.copy_result().sorted(), solo[i], f"replay {rep} sample {i}")
+    for h in handles:
+        h.destroy()
+
+
 # ------------------------------------------------------------------ full-size sampled parity
 
 @pytest.mark.slow
