@@ -80,7 +80,8 @@ typedef struct {
   uint64_t staging_bytes;     /* device staging buffer for host inputs (0: 256 MiB) */
   /* Launch shape (0 = library default; chosen by the autotuner per GPU and size class). */
   uint32_t block_threads;     /* threads per CTA of the counting kernels: 64..256, x32 */
-  uint32_t windows_per_thread;/* window starts one thread handles per tile: 1, 2, 4 or 8 */
+  uint32_t windows_per_thread;/* window starts one thread handles per tile: 1, 2, 4 or 8
+                                 (with partitions: records per thread, 4 or 8 -> 4, else 2) */
   uint32_t ctas_per_sm;       /* persistent grid = SMs x ctas_per_sm (0: occupancy bound) */
   uint32_t warp_aggregate;    /* 1: merge identical keys inside a warp before the atomics */
   /* Owner-computes partition (Section 5.1: a deterministic k-mer -> owner map makes every

@@ -169,7 +169,7 @@ int derive(const kma_params* p, Derived& d) {
   d.bit_words = pos / 64 + 4;
   d.mark_words = pos / 32 + 4;
   d.staging = p->staging_bytes ? p->staging_bytes : kDefaultStaging;
-  d.plan.device_bytes = d.codes_words * 8 + 2 * d.bit_words * 8 + d.mark_words * 4 +
+  d.plan.device_bytes = 2 * d.codes_words * 8 + 2 * d.bit_words * 8 + d.mark_words * 4 +
                         d.plan.bloom_words * 8 + d.plan.table_slots * sizeof(Slot) +
                         sizeof(DevStatus) + 2 * (2 * d.staging + (d.staging / 16 + 2) * 8);
   if (d.P > 1) d.plan.device_bytes += (p->max_bases + p->max_bases / 16) * d.rec_bytes;
@@ -217,6 +217,7 @@ struct kma_handle {
   unsigned prefetch = 1;
 
   u64* codes = nullptr;
+  u64* rcodes = nullptr;
   u64* inv = nullptr;
   u64* hq = nullptr;
   unsigned* marks = nullptr;
@@ -319,7 +320,7 @@ void free_records(kma_handle* h) {
 
 void free_all(kma_handle* h) {
   free_records(h);
-  dfree(h, h->codes); dfree(h, h->inv); dfree(h, h->hq); dfree(h, h->marks);
+  dfree(h, h->codes); dfree(h, h->rcodes); dfree(h, h->inv); dfree(h, h->hq); dfree(h, h->marks);
   dfree(h, h->bloom); dfree(h, h->table); dfree(h, h->status);
   for (int i = 0; i < 2; ++i) { dfree(h, h->stage_seq[i]); dfree(h, h->stage_qual[i]); dfree(h, h->stage_offs[i]); }
   dfree(h, h->out_keys); dfree(h, h->out_counts); dfree(h, h->out_ext); dfree(h, h->out_codes);
@@ -350,6 +351,7 @@ int clear_state(kma_handle* h) {
   // read by windows near the end, and those must read as invalid.
   KMA_CUDA(cudaMemsetAsync(h->inv, 0xFF, h->d.bit_words * 8, h->stream));
   KMA_CUDA(cudaMemsetAsync(h->codes, 0, h->d.codes_words * 8, h->stream));
+  KMA_CUDA(cudaMemsetAsync(h->rcodes, 0xFF, h->d.codes_words * 8, h->stream));
   KMA_CUDA(cudaMemsetAsync(h->hq, 0, h->d.bit_words * 8, h->stream));
   h->q_used = h->reads_used = h->bases_used = 0;
   h->finalized = false;
@@ -386,7 +388,7 @@ int read_status(kma_handle* h) {
 PassDesc pass_desc(kma_handle* h, unsigned mode, u64 q0, u64 q1) {
   PassDesc d;
   std::memset(&d, 0, sizeof(d));
-  d.codes = h->codes; d.inv = h->inv; d.hq = h->hq; d.marks = h->marks;
+  d.codes = h->codes; d.rcodes = h->rcodes; d.inv = h->inv; d.hq = h->hq; d.marks = h->marks;
   d.bloom = h->bloom; d.table = h->table; d.status = h->status;
   d.bloom_words = h->d.plan.bloom_words; d.slots = h->d.plan.table_slots;
   d.q0 = q0; d.q1 = q1;
@@ -413,7 +415,7 @@ int reserve_batch(kma_handle* h, u64 n_reads, u64 n_bases, PackDesc& pd, u64& q0
   q0 = h->q_used;
   std::memset(&pd, 0, sizeof(pd));
   pd.n_reads = n_reads; pd.n_bases = n_bases; pd.q0 = q0; pd.n_pos = n_pos;
-  pd.codes = h->codes; pd.inv = h->inv; pd.hq = h->hq; pd.status = h->status;
+  pd.codes = h->codes; pd.rcodes = h->rcodes; pd.inv = h->inv; pd.hq = h->hq; pd.status = h->status;
   pd.qual_min = (unsigned)h->p.qual_offset + (unsigned)h->p.qual_threshold;
   h->q_used += n_pos;
   h->reads_used += n_reads;
@@ -435,6 +437,7 @@ PartGeom part_geom(kma_handle* h) {
   g.canonical = h->p.canonical;
   g.n_parts = h->p.n_parts > 1 ? h->p.n_parts : 1;
   g.part = h->p.n_parts > 1 ? h->p.part : 0;
+  g.rpt = h->p.windows_per_thread >= 4 ? 4 : 2;
   return g;
 }
 
@@ -458,7 +461,7 @@ int first_pass(kma_handle* h, u64 q0, u64 n_pos, u64 n_reads, u64 n_bases, cudaS
   }
   const PartGeom g = part_geom(h);
   PartWindows w;
-  w.codes = h->codes; w.inv = h->inv; w.hq = h->hq;
+  w.codes = h->codes; w.rcodes = h->rcodes; w.inv = h->inv; w.hq = h->hq;
   w.q0 = q0; w.q1 = q0 + n_pos;
   const u64 P = h->d.P, k = h->p.k;
   // Bucket capacity from the window count of reads of length >= k (exact for such reads);
@@ -573,7 +576,8 @@ int kmer_analysis_create(const kma_params* params, void* cuda_stream, kma_handle
   if ((rc = get_pool(h->device, &h->pool))) { delete h; return rc; }
   choose_shape(h);
   h->stage_offs_cap = d.staging / 16 + 2;
-  if ((rc = dalloc(h, &h->codes, d.codes_words)) || (rc = dalloc(h, &h->inv, d.bit_words)) ||
+  if ((rc = dalloc(h, &h->codes, d.codes_words)) || (rc = dalloc(h, &h->rcodes, d.codes_words)) ||
+      (rc = dalloc(h, &h->inv, d.bit_words)) ||
       (rc = dalloc(h, &h->hq, d.bit_words)) || (rc = dalloc(h, &h->marks, d.mark_words)) ||
       (rc = dalloc(h, &h->bloom, d.plan.bloom_words)) ||
       (rc = dalloc(h, &h->table, d.plan.table_slots)) || (rc = dalloc(h, &h->status, 1))) {

@@ -24,12 +24,14 @@ __device__ __forceinline__ u64 key_hash(u64 lo, u64 hi) {
   return fmix64(lo ^ fmix64(hi + 0x9e3779b97f4a7c15ull));
 }
 
-// Everything derived from the 64-bit key hash h uses cheap 32-bit slices of h and of one more
-// product g = h * phi (golden-ratio constant), instead of further 64-bit mixes:
-//   on-chip partition   high 32 bits of h     (part_of)
-//   Bloom word          low 32 bits of h      (bloom_index; the filter has < 2^32 words)
-//   table slot          high 32 bits of g     (table_index; < 2^32 slots per partition)
-//   Bloom bit positions 6-bit fields of g     (bloom_mask)
+// Everything derived from the 64-bit key hash h uses cheap 32-bit slices of h and of two
+// more products, instead of further 64-bit mixes:
+//   on-chip partition   high 32 bits of h                  (part_of)
+//   Bloom word          low 32 bits of h                   (bloom_index; < 2^32 words)
+//   table slot          high 32 bits of h * phi            (table_index; < 2^32 slots per part)
+//   Bloom bit positions 6-bit fields from the top of (h ^ h >> 32) * c   (bloom_mask)
+// The bit positions must not depend on the low bits of h alone: those also pick the word, and
+// keys sharing a word would then share most of their bits (a much higher false-positive rate).
 __device__ __forceinline__ u64 scramble(u64 h) { return h * 0x9e3779b97f4a7c15ull; }
 __device__ __forceinline__ u64 table_index(u64 h, u64 slots) {
   return __umulhi((unsigned)(scramble(h) >> 32), (unsigned)slots);
@@ -48,9 +50,9 @@ __device__ __forceinline__ unsigned part_of(u64 h, unsigned P) {
 }
 
 __device__ __forceinline__ u64 bloom_mask(u64 h, unsigned nbits) {
-  const u64 g = scramble(h);
+  const u64 g = (h ^ (h >> 32)) * 0xd6e8feb86659fd93ull;
   u64 m = 0;
-  for (unsigned i = 0; i < nbits; ++i) m |= 1ull << ((g >> (6 * i)) & 63);
+  for (unsigned i = 0; i < nbits; ++i) m |= 1ull << ((g >> (58 - 6 * i)) & 63);
   return m;
 }
 
@@ -119,31 +121,50 @@ struct Window {
   bool lu, ru;       // usable (exists, A/C/G/T, Phred >= threshold)
 };
 
+// (a:b) << s, top 64 bits, for 0 <= s < 64.
+__device__ __forceinline__ u64 fshl(u64 a, u64 b, unsigned s) { return s ? (a << s) | (b >> (64 - s)) : a; }
+// (b:a) >> s, low 64 bits, for 0 <= s < 64.
+__device__ __forceinline__ u64 fshr(u64 a, u64 b, unsigned s) { return s ? (a >> s) | (b << (64 - s)) : a; }
+
 // Window starting at arena position q: returns false if any of its k positions is invalid.
-__device__ __forceinline__ bool load_window(const u64* codes, const u64* inv, const u64* hq,
-                                            unsigned k, unsigned canonical, u64 q, Window& w) {
+// The forward k-mer is read MSB-first from `codes`, its reverse complement LSB-first from
+// `rcodes` (both one funnel shift per 64-bit word), the canonical key is the smaller.
+__device__ __forceinline__ bool load_window(const u64* codes, const u64* rcodes, const u64* inv,
+                                            const u64* hq, unsigned k, unsigned canonical, u64 q,
+                                            Window& w) {
   const u64 v = q >> 6;
   const unsigned t = (unsigned)(q & 63);
-  u64 x = inv[v] << t;
-  if (t) x |= inv[v + 1] >> (64 - t);
-  if (x >> (64 - k)) return false;
+  if (fshl(inv[v], inv[v + 1], t) >> (64 - k)) return false;
 
   const u64 wi = q >> 5;
   const unsigned s = 2 * (unsigned)(q & 31);
-  const u64 a = codes[wi], b = codes[wi + 1], c = codes[wi + 2];
-  u128 top = ((u128)a << 64) | (u128)b;
-  if (s) top = (top << s) | (u128)(c >> (64 - s));
-  const u128 fw = top >> (128 - 2 * k);
-  const u64 flo = (u64)fw, fhi = (u64)(fw >> 64);
+  const u64 a = codes[wi], b = codes[wi + 1];
+  const u64 top = fshl(a, b, s);  // first 32 bases of the window, MSB-first
+  u64 flo, fhi, rlo, rhi;
+  const u64 r0 = rcodes[wi], r1 = rcodes[wi + 1];
+  const u64 bot = fshr(r0, r1, s);  // reverse complement, low 64 bits
+  if (k > 32) {
+    const u64 c = codes[wi + 2];
+    const u64 mid = fshl(b, c, s);
+    const unsigned sh = 128 - 2 * k;  // 2 .. 62
+    flo = (mid >> sh) | (top << (64 - sh));
+    fhi = top >> sh;
+    const u64 r2 = rcodes[wi + 2];
+    rlo = bot;
+    rhi = fshr(r1, r2, s) & ((1ull << (2 * k - 64)) - 1);
+  } else {
+    flo = top >> (64 - 2 * k);
+    fhi = 0;
+    rlo = k == 32 ? bot : bot & ((1ull << (2 * k)) - 1);
+    rhi = 0;
+  }
 
   // Extension bases: position q-1 (before) and q+k (after).
   const bool bu = q > 0 && bit_at(hq, q - 1);
   const bool au = bit_at(hq, q + k) != 0;
   const unsigned bb = q > 0 ? code_at(codes, q - 1) : 0u;
-  const unsigned ab = (unsigned)(top >> (126 - 2 * k)) & 3u;  // the base right after the window
+  const unsigned ab = code_at(codes, q + k);
 
-  u64 rlo, rhi;
-  revcomp(flo, fhi, k, rlo, rhi);
   const bool forward = !canonical || (fhi < rhi) || (fhi == rhi && flo <= rlo);
   if (forward) {
     w.lo = flo; w.hi = fhi;
@@ -158,7 +179,7 @@ __device__ __forceinline__ bool load_window(const u64* codes, const u64* inv, co
 }
 
 __device__ __forceinline__ bool load_window(const PassDesc& D, u64 q, Window& w) {
-  return load_window(D.codes, D.inv, D.hq, D.k, D.canonical, q, w);
+  return load_window(D.codes, D.rcodes, D.inv, D.hq, D.k, D.canonical, q, w);
 }
 
 // ------------------------------------------------------------------ table

@@ -7,6 +7,9 @@
 //                      two reads and the bases before/after a read are never usable.
 //     codes  u64[arena/32]  2 bits per position, first position in the two most significant
 //                           bits (A0 C1 G2 T3; 0 for invalid positions)
+//     rcodes u64[arena/32]  complemented codes (3 - code), first position in the two LEAST
+//                           significant bits: bits [2i, 2i+2k) of consecutive words read as
+//                           one number are the reverse complement of the window at i
 //     inv    u64[arena/64]  1 = position is not A/C/G/T (separator, N, padding), MSB first
 //     hq     u64[arena/64]  1 = A/C/G/T with Phred >= qual_threshold, MSB first
 //     marks  u32[arena/32]  Bloom pass: 1 = this window was the first sighting of its k-mer
@@ -52,6 +55,7 @@ struct DevStatus {
 // Per-sample view the pass kernels need. Passed by value inside kernel parameters.
 struct PassDesc {
   const unsigned long long* codes;
+  const unsigned long long* rcodes;
   const unsigned long long* inv;
   const unsigned long long* hq;
   unsigned int* marks;
@@ -94,6 +98,7 @@ struct PackDesc {
   unsigned long long n_pos;           // n_bases + n_reads, rounded up to a multiple of 64
   unsigned long long chunk_begin;     // prefix of 256-word pack chunks over the batch
   unsigned long long* codes;
+  unsigned long long* rcodes;
   unsigned long long* inv;
   unsigned long long* hq;
   DevStatus* status;
@@ -156,10 +161,13 @@ struct PartGeom {
   unsigned int canonical;
   unsigned int n_parts;         // multi-GPU owner filter (as PassDesc)
   unsigned int part;
+  unsigned int rpt;             // records per thread in flight in the record passes (2 or 4)
+  unsigned int pad;
 };
 
 struct PartWindows {
   const unsigned long long* codes;
+  const unsigned long long* rcodes;
   const unsigned long long* inv;
   const unsigned long long* hq;
   unsigned long long q0, q1;    // window starts of one count() batch (multiples of 64)

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
       u64 r = D.n_reads ? read_at(off, o0, D.n_reads, s_r0, p0) : 0;
       u64 rs = D.n_reads ? off[r] - o0 + r : 0;
       u64 re = D.n_reads ? off[r + 1] - o0 + r : 0;
-      u64 c0 = 0, c1 = 0, inv = 0, hq = 0;
+      u64 c0 = 0, c1 = 0, r0 = 0, r1 = 0, inv = 0, hq = 0;
 #pragma unroll 4
       for (int i = 0; i < 64; ++i) {
         const u64 p = p0 + i;
@@ -329,18 +329,25 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
           code = ch == 'C' ? 1u : ch == 'G' ? 2u : ch == 'T' ? 3u : 0u;
           good = valid && (unsigned)s_qual[leadq + (unsigned)(bidx - b0)] >= D.qual_min;
         }
-        if (i < 32) c0 |= (u64)code << (62 - 2 * i);
-        else c1 |= (u64)code << (62 - 2 * (i - 32));
+        if (i < 32) {
+          c0 |= (u64)code << (62 - 2 * i);
+          r0 |= (u64)(3u - code) << (2 * i);
+        } else {
+          c1 |= (u64)code << (62 - 2 * (i - 32));
+          r1 |= (u64)(3u - code) << (2 * (i - 32));
+        }
         inv |= (u64)(!valid) << (63 - i);
         hq |= (u64)good << (63 - i);
       }
       const u64 gw = (D.q0 >> 6) + w;
       reinterpret_cast<ulonglong2*>(D.codes)[gw] = make_ulonglong2(c0, c1);
+      reinterpret_cast<ulonglong2*>(D.rcodes)[gw] = make_ulonglong2(r0, r1);
       D.inv[gw] = inv;
       D.hq[gw] = hq;
     } else if (w < w1) {
       const u64 gw = (D.q0 >> 6) + w;
       reinterpret_cast<ulonglong2*>(D.codes)[gw] = make_ulonglong2(0, 0);
+      reinterpret_cast<ulonglong2*>(D.rcodes)[gw] = make_ulonglong2(~0ull, ~0ull);
       D.inv[gw] = ~0ull;
       D.hq[gw] = 0;
     }

@@ -40,7 +40,8 @@ constexpr u64 kBitsBytes = align256((kMaxPositions / 64 + 4) * 8);
 constexpr u64 kStatusBytes = align256(sizeof(DevStatus));
 constexpr u64 kTableBytes = kMaxSlots * sizeof(Slot);
 constexpr u64 kOffCodes = 0;
-constexpr u64 kOffInv = kOffCodes + kCodesBytes;
+constexpr u64 kOffRcodes = kOffCodes + kCodesBytes;
+constexpr u64 kOffInv = kOffRcodes + kCodesBytes;
 constexpr u64 kOffHq = kOffInv + kBitsBytes;
 constexpr u64 kOffStatus = kOffHq + kBitsBytes;
 constexpr u64 kOffTable = kOffStatus + kStatusBytes;
@@ -100,6 +101,7 @@ extern "C" int kmer_analysis_count_small_noalloc(const kma_params* params, const
   if ((rc = set_up(dev, &base))) return rc;
 
   u64* d_codes = reinterpret_cast<u64*>(base + kOffCodes);
+  u64* d_rcodes = reinterpret_cast<u64*>(base + kOffRcodes);
   u64* d_inv = reinterpret_cast<u64*>(base + kOffInv);
   u64* d_hq = reinterpret_cast<u64*>(base + kOffHq);
   DevStatus* d_status = reinterpret_cast<DevStatus*>(base + kOffStatus);
@@ -112,6 +114,7 @@ extern "C" int kmer_analysis_count_small_noalloc(const kma_params* params, const
   // Clear what must start empty: the array keeps the previous call's contents.
   if ((rc = check(cudaMemsetAsync(d_status, 0, sizeof(DevStatus), stream)))) return rc;
   if ((rc = check(cudaMemsetAsync(d_codes, 0, codes_words * 8, stream)))) return rc;
+  if ((rc = check(cudaMemsetAsync(d_rcodes, 0xFF, codes_words * 8, stream)))) return rc;
   if ((rc = check(cudaMemsetAsync(d_inv, 0xFF, bit_words * 8, stream)))) return rc;
   if ((rc = check(cudaMemsetAsync(d_hq, 0, bit_words * 8, stream)))) return rc;
   if ((rc = check(launch_table_init(d_table, slots, stream)))) return rc;
@@ -132,6 +135,7 @@ extern "C" int kmer_analysis_count_small_noalloc(const kma_params* params, const
     pd.n_pos = n_pos;
     pd.chunk_begin = 0;
     pd.codes = d_codes;
+    pd.rcodes = d_rcodes;
     pd.inv = d_inv;
     pd.hq = d_hq;
     pd.status = d_status;
@@ -144,6 +148,7 @@ extern "C" int kmer_analysis_count_small_noalloc(const kma_params* params, const
     b.n = 1;
     PassDesc& d = b.d[0];
     d.codes = d_codes;
+    d.rcodes = d_rcodes;
     d.inv = d_inv;
     d.hq = d_hq;
     d.table = d_table;

@@ -29,7 +29,7 @@ __device__ __forceinline__ void window_of(unsigned char inf, Window& w) {
 // Window at q of the batch, canonical key hashed, owner filter applied.
 __device__ __forceinline__ bool part_window(const PartGeom& G, const PartWindows& W, u64 q,
                                             Window& w, u64& h) {
-  if (!load_window(W.codes, W.inv, W.hq, G.k, G.canonical, q, w)) return false;
+  if (!load_window(W.codes, W.rcodes, W.inv, W.hq, G.k, G.canonical, q, w)) return false;
   h = key_hash(w.lo, w.hi);
   if (G.n_parts > 1 && owner_of(h, G.n_parts) != G.part) return false;
   return true;
@@ -143,13 +143,12 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const __grid
 // Tiles walk the buckets in partition order (then the overflow area), so at any moment the
 // CTAs work on one or two partitions whose sub-filter and sub-table sit in L2.
 
-constexpr int kRecPerThread = 2;
-constexpr int kRecTile = kPartThreads * kRecPerThread;
 
-template <int KW>
+template <int KW, int kRecPerThread>
 __global__ void __launch_bounds__(kPartThreads) part_pass_kernel(const __grid_constant__ PartGeom G,
                                                                  const __grid_constant__ PartRecords R,
                                                                  unsigned mode) {
+  constexpr int kRecTile = kPartThreads * kRecPerThread;
   const unsigned lane = threadIdx.x & 31;
   const u64 tpb = (R.cap + kRecTile - 1) / kRecTile;          // tiles per bucket
   const u64 otiles = (R.ocap + kRecTile - 1) / kRecTile;
@@ -187,6 +186,10 @@ __global__ void __launch_bounds__(kPartThreads) part_pass_kernel(const __grid_co
       p[j] = 0;
       inf[j] = 0;
       if (act[j]) {
+        inf[j] = (unsigned char)ld_stream(R.info + i, pol);
+        if (mode == kModeRecount && !(inf[j] & kInfoFirst)) act[j] = false;  // keys not needed
+      }
+      if (act[j]) {
         if (KW == 1) {
           w[j].lo = ld_stream(reinterpret_cast<const u64*>(R.keys) + i, pol);
           w[j].hi = 0;
@@ -195,9 +198,7 @@ __global__ void __launch_bounds__(kPartThreads) part_pass_kernel(const __grid_co
           w[j].lo = kk.x;
           w[j].hi = kk.y;
         }
-        inf[j] = (unsigned char)ld_stream(R.info + i, pol);
         window_of(inf[j], w[j]);
-        if (mode == kModeRecount && !(inf[j] & kInfoFirst)) act[j] = false;
         h[j] = key_hash(w[j].lo, w[j].hi);
         p[j] = part_of(h[j], G.P);
       }
@@ -285,16 +286,25 @@ cudaError_t launch_part_scatter(const PartGeom& g, const PartWindows& w, const P
   return cudaGetLastError();
 }
 
+template <int KW, int RPT>
+static cudaError_t launch_pass_rt(const PartGeom& g, const PartRecords& r, unsigned mode, cudaStream_t stream,
+                                  int num_sms) {
+  constexpr int tile = kPartThreads * RPT;
+  const u64 tiles = (u64)g.P * ((r.cap + tile - 1) / tile) + (r.ocap + tile - 1) / tile;
+  if (tiles == 0) return cudaSuccess;
+  u64 grid = grid_for((const void*)part_pass_kernel<KW, RPT>, kPartThreads, 0, num_sms);
+  if (grid > tiles) grid = tiles;
+  part_pass_kernel<KW, RPT><<<(unsigned)grid, kPartThreads, 0, stream>>>(g, r, mode);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_part_pass(const PartGeom& g, const PartRecords& r, unsigned mode, cudaStream_t stream,
                              int num_sms) {
-  const u64 tiles = (u64)g.P * ((r.cap + kRecTile - 1) / kRecTile) + (r.ocap + kRecTile - 1) / kRecTile;
-  if (tiles == 0) return cudaSuccess;
-  const void* fn = g.k > 32 ? (const void*)part_pass_kernel<2> : (const void*)part_pass_kernel<1>;
-  u64 grid = grid_for(fn, kPartThreads, 0, num_sms);
-  if (grid > tiles) grid = tiles;
-  if (g.k > 32) part_pass_kernel<2><<<(unsigned)grid, kPartThreads, 0, stream>>>(g, r, mode);
-  else part_pass_kernel<1><<<(unsigned)grid, kPartThreads, 0, stream>>>(g, r, mode);
-  return cudaGetLastError();
+  if (g.rpt >= 4)
+    return g.k > 32 ? launch_pass_rt<2, 4>(g, r, mode, stream, num_sms)
+                    : launch_pass_rt<1, 4>(g, r, mode, stream, num_sms);
+  return g.k > 32 ? launch_pass_rt<2, 2>(g, r, mode, stream, num_sms)
+                  : launch_pass_rt<1, 2>(g, r, mode, stream, num_sms);
 }
 
 }  // namespace kma
