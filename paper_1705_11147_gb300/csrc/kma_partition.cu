@@ -39,18 +39,23 @@ constexpr int kPartThreads = 256;
 
 // ------------------------------------------------------------------ scatter
 //
-// One tile = kPartThreads * kScatterWpt consecutive window starts. Phase 1 extracts the
-// windows, stages key + info in shared memory and ranks each window inside its partition for
-// this tile (shared-memory atomics). Phase 2 reserves each partition's run in its bucket
-// with one global atomic per partition present (split into bucket part and overflow part).
-// Phase 3 writes the records with an evict-first L2 policy.
+// One tile = kPartThreads * kScatterWpt consecutive window starts.
+//  1. extract the windows, stage key + info in shared memory, rank each window inside its
+//     partition for this tile (shared-memory atomics);
+//  2. exclusive scan of the per-partition counts (the tile's records sorted by partition) and
+//     one global reservation per partition present (bucket part, overflow part);
+//  3. permute the staged records into partition order and write them out: consecutive
+//     threads write consecutive records of the same bucket, so the stores coalesce.
 
-constexpr int kScatterWpt = 8;
-constexpr int kScatterTile = kPartThreads * kScatterWpt;
+constexpr int kScatterWpt = 16;
+constexpr int kScatterTile = kPartThreads * kScatterWpt;  // 4096 (< 2^13: ranks and slots fit)
 
 __host__ __device__ constexpr size_t scatter_smem(unsigned P, int kw) {
-  return (size_t)kScatterTile * (kw * 8) + kScatterTile +   // staged keys, info
-         (size_t)P * 4 * 3 + (size_t)P * 8 + 64;             // cnt, base, n1 (u32), obase (u64)
+  return (size_t)kScatterTile * (kw * 8) +   // staged keys
+         (size_t)kScatterTile +              // staged info
+         (size_t)kScatterTile * 4 +          // sorted order: slot | partition << 16
+         (size_t)P * (4 + 4 + 4 + 8 + 8) +   // cnt, off, n1, gbase, obase
+         256;                                // warp sums, tile total, alignment
 }
 
 template <int KW>
@@ -58,22 +63,25 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const __grid
                                                                     const __grid_constant__ PartWindows W,
                                                                     const __grid_constant__ PartRecords R) {
   extern __shared__ __align__(16) unsigned char s_raw[];
-  u64* s_keys = reinterpret_cast<u64*>(s_raw);                             // [tile * KW]
-  unsigned char* s_info = s_raw + (size_t)kScatterTile * KW * 8;            // [tile]
-  unsigned* s_cnt = reinterpret_cast<unsigned*>(s_info + kScatterTile);     // [P]
-  unsigned* s_base = s_cnt + G.P;                                           // [P] bucket offset
-  unsigned* s_n1 = s_base + G.P;                                            // [P] records to bucket
-  u64* s_obase = reinterpret_cast<u64*>((reinterpret_cast<uintptr_t>(s_n1 + G.P) + 7) & ~uintptr_t(7));
-  const unsigned lane = threadIdx.x & 31;
+  const unsigned P = G.P;
+  u64* s_keys = reinterpret_cast<u64*>(s_raw);                                   // [tile * KW]
+  u64* s_gbase = s_keys + (size_t)kScatterTile * KW;                             // [P]
+  u64* s_obase = s_gbase + P;                                                    // [P]
+  unsigned* s_order = reinterpret_cast<unsigned*>(s_obase + P);                  // [tile]
+  unsigned* s_cnt = s_order + kScatterTile;                                      // [P]
+  unsigned* s_off = s_cnt + P;                                                   // [P]
+  unsigned* s_n1 = s_off + P;                                                    // [P]
+  unsigned* s_wsum = s_n1 + P;                                                   // [8 + 1]
+  unsigned char* s_info = reinterpret_cast<unsigned char*>(s_wsum + 16);         // [tile]
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u64 n_tiles = (W.q1 - W.q0 + kScatterTile - 1) / kScatterTile;
   const u64 pol = policy_evict_first();
-  const unsigned P = G.P;
   u64 acc_valid = 0;
   for (unsigned p = threadIdx.x; p < P; p += blockDim.x) s_cnt[p] = 0;
   __syncthreads();
   for (u64 t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     // 1: windows -> staged records, rank inside the partition
-    unsigned pr[kScatterWpt];  // partition (high 16 bits... packed below) | rank
+    unsigned pr[kScatterWpt];  // partition << 13 | rank, or ~0u
 #pragma unroll
     for (int j = 0; j < kScatterWpt; ++j) {
       const unsigned slot = j * kPartThreads + threadIdx.x;
@@ -85,53 +93,87 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const __grid
       acc_valid += __popc(__ballot_sync(0xffffffffu, ok));
       if (ok) {
         const unsigned p = part_of(h, P);
-        const unsigned r = atomicAdd(&s_cnt[p], 1u);
-        pr[j] = (p << 13) | r;  // P <= 4096 (12 bits), rank < 8192 (13 bits)
+        pr[j] = (p << 13) | atomicAdd(&s_cnt[p], 1u);
         s_keys[(size_t)slot * KW] = w.lo;
         if (KW == 2) s_keys[(size_t)slot * KW + 1] = w.hi;
         s_info[slot] = info_of(w);
       }
     }
     __syncthreads();
-    // 2: reserve runs (bucket first, the rest in the overflow area); counters reset for
-    //    the next tile
+    // 2a: exclusive scan of the counts (each thread a contiguous chunk of partitions)
+    const unsigned per = (P + kPartThreads - 1) / kPartThreads;
+    const unsigned p0 = threadIdx.x * per, p1 = min(P, p0 + per);
+    unsigned local = 0;
+    for (unsigned p = p0; p < p1; ++p) local += s_cnt[p];
+    unsigned incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (unsigned)o) incl += v;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned run = 0;
+      for (int x = 0; x < kPartThreads / 32; ++x) {
+        const unsigned v = s_wsum[x];
+        s_wsum[x] = run;
+        run += v;
+      }
+      s_wsum[8] = run;  // records in this tile
+    }
+    __syncthreads();
+    unsigned run = s_wsum[warp] + incl - local;
+    for (unsigned p = p0; p < p1; ++p) {
+      s_off[p] = run;
+      run += s_cnt[p];
+    }
+    // 2b: reserve each partition's run: bucket first, the rest in the overflow area
     for (unsigned p = threadIdx.x; p < P; p += blockDim.x) {
       const unsigned c = s_cnt[p];
       if (c) {
         const u64 b = atomicAdd(&R.fill[p], (u64)c);
         const u64 room = b < R.cap ? R.cap - b : 0;
         const unsigned n1 = (unsigned)(room < c ? room : c);
-        s_base[p] = (unsigned)(b < R.cap ? b : 0);
+        s_gbase[p] = (u64)p * R.cap + (b < R.cap ? b : 0);
         s_n1[p] = n1;
         s_obase[p] = n1 < c ? atomicAdd(&R.fill[P], (u64)(c - n1)) : 0;
       }
     }
     __syncthreads();
-    for (unsigned p = threadIdx.x; p < P; p += blockDim.x) s_cnt[p] = 0;
-    // 3: write the records
+    // 3a: sorted order (partition-major) of the staged records
 #pragma unroll
     for (int j = 0; j < kScatterWpt; ++j) {
       if (pr[j] == 0xFFFFFFFFu) continue;
-      const unsigned slot = j * kPartThreads + threadIdx.x;
       const unsigned p = pr[j] >> 13, r = pr[j] & 8191u;
-      u64 i;
+      s_order[s_off[p] + r] = (j * kPartThreads + threadIdx.x) | (p << 16);
+    }
+    for (unsigned p = threadIdx.x; p < P; p += blockDim.x) s_cnt[p] = 0;  // for the next tile
+    __syncthreads();
+    // 3b: write out in sorted order (coalesced runs per bucket)
+    const unsigned total = s_wsum[8];
+    for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
+      const unsigned e = s_order[i];
+      const unsigned slot = e & 0xFFFFu, p = e >> 16;
+      const unsigned r = i - s_off[p];
+      u64 gi;
       if (r < s_n1[p]) {
-        i = (u64)p * R.cap + s_base[p] + r;
+        gi = s_gbase[p] + r;
       } else {
         const u64 o = s_obase[p] + (r - s_n1[p]);
         if (o >= R.ocap) {  // overflow area full: reported, never dropped silently
           atomicOr(&G.status->flags, kFlagFull);
           continue;
         }
-        i = (u64)P * R.cap + o;
+        gi = (u64)P * R.cap + o;
       }
       if (KW == 1) {
-        st_stream(reinterpret_cast<u64*>(R.keys) + i, s_keys[slot], pol);
+        st_stream(reinterpret_cast<u64*>(R.keys) + gi, s_keys[slot], pol);
       } else {
-        st_stream(reinterpret_cast<ulonglong2*>(R.keys) + i,
+        st_stream(reinterpret_cast<ulonglong2*>(R.keys) + gi,
                   make_ulonglong2(s_keys[(size_t)slot * 2], s_keys[(size_t)slot * 2 + 1]), pol);
       }
-      st_stream(R.info + i, s_info[slot], pol);
+      st_stream(R.info + gi, s_info[slot], pol);
     }
     __syncthreads();  // staged records and per-partition runs are reused by the next tile
   }
