@@ -178,51 +178,83 @@ def cpu_baseline(rs, budget_s: float = 15.0, threads: int | None = None) -> dict
     import oracle
     threads = threads or os.cpu_count() or 1
     k = rs.meta["params"]["k"]
-
-    def prefix(n):
-        n = min(n, rs.n_reads)
-        offs = rs.offsets[: n + 1]
-        return rs.seq[: int(offs[-1])], rs.qual[: int(offs[-1])], offs
-
     p = dict(rs.meta["params"])
     p.pop("bloom_fpr", None)
-    n = 20000
-    s, q, o = prefix(n)
+    n = oracle_sample_reads(rs, budget_s, threads)
+    offs = rs.offsets[: n + 1]
     t0 = time.perf_counter()
-    r = oracle.run(s, q, o, threads=threads, **p)
-    dt = time.perf_counter() - t0
-    rate = r.valid_windows / max(dt, 1e-9)
-    n = int(min(rs.n_reads, max(n, n * budget_s / max(dt, 1e-6))))
-    s, q, o = prefix(n)
-    t0 = time.perf_counter()
-    r = oracle.run(s, q, o, threads=threads, **p)
+    r = oracle.run(rs.seq[: int(offs[-1])], rs.qual[: int(offs[-1])], offs, threads=threads, **p)
     dt = time.perf_counter() - t0
     return {"value": r.valid_windows / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"first {n} of {rs.n_reads} reads ({r.valid_windows} windows, k={k}), "
                       f"{dt:.1f} s wall on {threads} threads",
-            "seconds": dt, "windows": int(r.valid_windows), "reads": n,
-            "calibration_rate": rate / 1e9}
+            "seconds": round(dt, 2), "windows": int(r.valid_windows), "reads": n}
 
 
 # ------------------------------------------------------------------ GPU arm
 
-def roofline(timing: dict, res_info, positions: int, peak_gbs: float, steps: int) -> dict:
-    """Dominant kernel: the first pass (Bloom test-and-set + table insert/update).
-    Algorithmic bytes per launch, 32-byte sectors, Bloom filter and table far larger than L2:
-      64 B per valid window  (Bloom word: sector read + write-back)
-     128 B per window whose k-mer the filter had seen (slot: key/count sector and extension
-           sector, each read + written back)
-     0.625 B per arena position (2-bit codes, invalid and quality bits read, marks written)."""
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+
+
+def kernel_source_digest(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1705_11147_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(summary: str, digest: str):
+    """DRAM bytes per unit recorded by an ncu capture (profiles/<summary>), or None when the
+    kernel sources changed since the capture."""
+    try:
+        text = open(os.path.join(PROFILE_DIR, summary)).read()
+    except OSError:
+        return None
+    vals = dict(line.split(":", 1) for line in text.splitlines()
+                if line.startswith(("kernel_source_digest:", "dram_bytes_per_unit:")))
+    if vals.get("kernel_source_digest", "").strip() != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_unit"])
+    except (KeyError, ValueError):
+        return None
+
+
+def roofline(timing: dict, res_info, positions: int, peak_gbs: float, plan_used, k: int) -> dict:
+    """Dominant kernel, algorithmic DRAM bytes per launch (32-byte sectors; Bloom filter and
+    table far larger than L2):
+    one table (pass_kernel, Bloom mode):
+      64 B per valid window (Bloom word sector read + write-back), 128 B per window whose k-mer
+      the filter had seen (slot key/count sector + extension sector, read + written back),
+      0.625 B per arena position (codes, reverse codes... read, marks written).
+    partitions (part_pass_kernel, Bloom mode):
+      per record (one per valid window) its key + info byte read (17 B, 9 B for k <= 32),
+      1 B per first sighting (flag written back), and each partition's Bloom sub-filter and
+      sub-table brought from HBM once and written back once: 2 x (filter + table bytes)."""
     W = int(res_info.valid_windows)
     F = int(timing["first_sightings"])
-    seen = W - F
-    algo_bytes = 64.0 * W + 128.0 * seen + 0.625 * positions
     ms = timing["ms_pass"] / max(timing["n_pass"], 1)
-    achieved = algo_bytes / (ms * 1e-3) / 1e9
+    if plan_used.partitions > 1:
+        rec = (16 if k > 32 else 8) + 1
+        struct_bytes = plan_used.bloom_words * 8 + plan_used.table_slots * 64
+        algo = float(W) * rec + F + 2.0 * struct_bytes
+        kernel, files, summary = ("part_pass_kernel (Bloom mode)", ["kma_partition.cu", "kma_device.cuh"],
+                                  "part_pass_kernel_large_200m.md")
+        units = W
+    else:
+        algo = 64.0 * W + 128.0 * (W - F) + 0.625 * positions
+        kernel, files, summary = ("pass_kernel (Bloom mode)", ["kma_kernels.cu", "kma_device.cuh"],
+                                  "pass_kernel_large_200m.md")
+        units = W
+    achieved = algo / (ms * 1e-3) / 1e9
+    per_unit = profiled_traffic(summary, kernel_source_digest(files))
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs, "unit": "GB/s",
-            "frac": round(achieved / peak_gbs, 4), "traffic": None,
-            "kernel": "pass_kernel (Bloom mode)", "ms_per_launch": round(ms, 3),
-            "algo_bytes_per_launch": int(algo_bytes), "peak_source": "of measured (hbm_gbs)"}
+            "frac": round(achieved / peak_gbs, 4),
+            "traffic": None if per_unit is None else int(per_unit * units),
+            "kernel": kernel, "ms_per_launch": round(ms, 3), "algo_bytes_per_launch": int(algo),
+            "peak_source": "of measured (hbm_gbs)"}
 
 
 def load_peak() -> float:
@@ -315,7 +347,7 @@ def run_ours(args, ws, rank, local):
         W_total = int(t.item())
     value = W_total / (ms_step * 1e-3) / 1e9
     positions = rs.n_bases + rs.n_reads
-    roof = roofline(timing, info, positions, load_peak(), args.steps)
+    roof = roofline(timing, info, positions, load_peak(), plan_used, k)
     kernel_ms = {k2[3:]: round(v / args.steps, 3) for k2, v in timing.items() if k2.startswith("ms_")}
     launches = int(timing["launches"])
 
@@ -425,7 +457,7 @@ def run_batched(args, ws, rank, local):
               torch.from_numpy(rs.offsets.astype(np.int64)).to(dev)) for rs in sets]
 
     def params(rs):
-        return make_handle_params(rs, partitions=1, **args.tuning)
+        return make_handle_params(rs, **args.tuning)
 
     handles = [KmerAnalysis(params(rs)) for rs in sets]
     g = BatchGraph(handles, reads)
@@ -552,20 +584,32 @@ def run_served(args, ws, rank, local):
 
 # ------------------------------------------------------------------ reference arm
 
+def oracle_sample_reads(rs, budget_s: float, threads: int) -> int:
+    """Reads of a prefix that takes the oracle about `budget_s` seconds (from a short
+    calibration on the first 20000 reads)."""
+    import oracle
+    p = dict(rs.meta["params"])
+    p.pop("bloom_fpr", None)
+    n = min(20000, rs.n_reads)
+    offs = rs.offsets[: n + 1]
+    t0 = time.perf_counter()
+    oracle.run(rs.seq[: int(offs[-1])], rs.qual[: int(offs[-1])], offs, threads=threads, **p)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    return int(min(rs.n_reads, max(n, n * budget_s / dt)))
+
+
 def run_reference(args, ws, rank):
     """The CPU oracle on the same workload, metric and unit; each step a bounded prefix of
-    the reads (rank 0 only)."""
+    the reads, sized so that warm-up + steps take about two minutes (rank 0 only)."""
     if rank != 0:
         return None
     import oracle
-    rs = synth.workload(args.workload, scale=args.scale)
+    rs = synth.workload(args.workload if args.workload in synth.WORKLOADS else "large_200m", scale=args.scale)
     threads = os.cpu_count() or 1
     p = dict(rs.meta["params"])
     p.pop("bloom_fpr", None)
-    # calibrate a prefix so that warmup + steps fit a few minutes
-    cal = cpu_baseline(rs, budget_s=max(5.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1))),
-                       threads=threads)
-    n = int(cal["reads"])
+    budget = max(3.0, min(15.0, 110.0 / max(args.steps + args.warmup, 1)))
+    n = oracle_sample_reads(rs, budget, threads)
     offs = rs.offsets[: n + 1]
     s, q = rs.seq[: int(offs[-1])], rs.qual[: int(offs[-1])]
     for _ in range(args.warmup):
@@ -579,7 +623,7 @@ def run_reference(args, ws, rank):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt * 1e3, 1), "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": args.workload, "k": p["k"], "sample_reads": n,
+            "config": {"workload": rs.meta["workload"], "k": p["k"], "sample_reads": n,
                        "sample_windows": int(r.valid_windows)},
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": threads,
                              "kind": "oracle", "sample": f"first {n} of {rs.n_reads} reads per step"},

@@ -262,42 +262,48 @@ def fetch_result(h: KmerAnalysis) -> capi.kma_result:
 
 
 class BatchGraph:
-    """Many samples in one CUDA graph: reset -> count_batch (one packing launch and one
-    persistent counting launch for all samples) -> finalize_batch_async (one recount and one
-    classification launch), captured once and replayed. `reads[i]` = (seq, qual, offsets)
-    CUDA tensors of handle i; all handles are moved to the capture stream."""
+    """Many samples in one CUDA graph. Samples counted in one table are packed and counted
+    together (one packing launch and one persistent counting launch), then recounted and
+    classified together (kmer_analysis_finalize_batch_async). Samples large enough to be
+    partitioned run their scatter/record passes one after another inside the same graph, each
+    finalized before the next starts, so only one sample's record buckets exist at a time.
+    Captured once, replayed per step. `reads[i]` = (seq, qual, offsets) CUDA tensors of
+    handle i; all handles are moved to the capture stream."""
 
     def __init__(self, handles: list[KmerAnalysis], reads: list[tuple], headroom: float = 1.25):
         torch = _torch()
-        assert 0 < len(handles) <= capi.KMA_MAX_BATCH and len(handles) == len(reads)
+        assert len(handles) == len(reads) and handles
         self.handles, self.reads = handles, reads
+        parts = [plan(h.params).partitions for h in handles]
+        self.small = [i for i, p in enumerate(parts) if p <= 1]
+        self.large = [i for i, p in enumerate(parts) if p > 1]
         self.stream = torch.cuda.Stream()
         for h in handles:
             h.set_stream(self.stream)
         # eager run: sizes the output buffers the captured finalize writes into
         with torch.cuda.stream(self.stream):
-            self._step_eager()
+            self._step(finalize_batch)
         for h in handles:
             reserve_output(h, int(h.result_info.table_keys * headroom) + 1024)
         before = sum(h.timings()["launches"] for h in handles)
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph, stream=self.stream):
-            self._step_async()
+            self._step(finalize_batch_async)
         self.stream.synchronize()
         # library kernels in the graph (the host counters tick once, at capture)
         self.kernels_per_replay = sum(h.timings()["launches"] for h in handles) - before
 
-    def _step_eager(self):
+    def _step(self, finalize):
         for h in self.handles:
             h.reset()
-        count_batch(self.handles, self.reads)
-        finalize_batch(self.handles)
-
-    def _step_async(self):
-        for h in self.handles:
-            h.reset()
-        count_batch(self.handles, self.reads)
-        finalize_batch_async(self.handles)
+        for c0 in range(0, len(self.small), capi.KMA_MAX_BATCH):
+            idx = self.small[c0:c0 + capi.KMA_MAX_BATCH]
+            hs = [self.handles[i] for i in idx]
+            count_batch(hs, [self.reads[i] for i in idx])
+            finalize(hs)
+        for i in self.large:
+            count_batch([self.handles[i]], [self.reads[i]])
+            finalize([self.handles[i]])
 
     def replay(self) -> None:
         """Launch the graph on the handles' stream (results are read from that stream)."""

@@ -335,8 +335,10 @@ def test_batch_graph_replay_equals_solo(gpu):
     from paper_1705_11147_gb300 import BatchGraph, KmerAnalysis, make_params
     specs = synth.batched_specs(9, scale=0.01)
     sets = [synth.sample_reads(s) for s in specs]
+    # one-table and partitioned handles mixed in one graph
     handles = [KmerAnalysis(make_params(k=51, min_depth=2, max_bases=rs.n_bases, max_reads=rs.n_reads,
-                                        expected_distinct=rs.n_bases, partitions=1)) for rs in sets]
+                                        expected_distinct=rs.n_bases, partitions=1 if i % 3 else 7))
+               for i, rs in enumerate(sets)]
     reads = [to_dev(gpu, rs) for rs in sets]
     g = BatchGraph(handles, reads)
     solo = [run_gpu(gpu, rs) for rs in sets]
