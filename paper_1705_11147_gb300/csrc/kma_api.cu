@@ -232,6 +232,10 @@ struct kma_handle {
   int stage_next = 0;
 
   u64 q_used = 0, reads_used = 0, bases_used = 0;
+  // Upper bound on the occurrences any one key can have collected since the last reset
+  // (windows counted in one table; bucket + overflow records per batch in partitioned
+  // mode). Below 2^32 no counter can wrap and the passes count with plain reductions.
+  u64 count_bound = 0;
   bool finalized = false;
   bool failed = false;
 
@@ -354,6 +358,7 @@ int clear_state(kma_handle* h) {
   KMA_CUDA(cudaMemsetAsync(h->rcodes, 0xFF, h->d.codes_words * 8, h->stream));
   KMA_CUDA(cudaMemsetAsync(h->hq, 0, h->d.bit_words * 8, h->stream));
   h->q_used = h->reads_used = h->bases_used = 0;
+  h->count_bound = 0;
   h->finalized = false;
   h->failed = false;
   std::memset(&h->res, 0, sizeof(h->res));
@@ -396,6 +401,7 @@ PassDesc pass_desc(kma_handle* h, unsigned mode, u64 q0, u64 q1) {
   d.mode = mode;
   d.n_parts = h->p.n_parts > 1 ? h->p.n_parts : 1;
   d.part = h->p.n_parts > 1 ? h->p.part : 0;
+  d.no_overflow = h->count_bound < (1ull << 32) ? 1u : 0u;
   return d;
 }
 
@@ -438,6 +444,8 @@ PartGeom part_geom(kma_handle* h) {
   g.n_parts = h->p.n_parts > 1 ? h->p.n_parts : 1;
   g.part = h->p.n_parts > 1 ? h->p.part : 0;
   g.rpt = h->p.windows_per_thread >= 4 ? 4 : 2;
+  g.wait_limit = 1u << 22;
+  g.no_overflow = h->count_bound < (1ull << 32) ? 1u : 0u;
   return g;
 }
 
@@ -448,6 +456,7 @@ PartGeom part_geom(kma_handle* h) {
 int first_pass(kma_handle* h, u64 q0, u64 n_pos, u64 n_reads, u64 n_bases, cudaStream_t st) {
   const unsigned mode = h->p.use_bloom ? kModeBloom : kModeCount;
   if (h->d.P <= 1) {
+    h->count_bound += n_pos;
     PassBatch b;
     std::memset(&b, 0, offsetof(PassBatch, d) + sizeof(PassDesc));
     b.n = 1;
@@ -459,18 +468,21 @@ int first_pass(kma_handle* h, u64 q0, u64 n_pos, u64 n_reads, u64 n_bases, cudaS
     return timed_launch(h, KMA_KERNEL_PASS, st, b.total_tiles > 0,
                         [&] { return launch_pass(b, h->shape, h->agg, st); });
   }
-  const PartGeom g = part_geom(h);
   PartWindows w;
   w.codes = h->codes; w.rcodes = h->rcodes; w.inv = h->inv; w.hq = h->hq;
   w.q0 = q0; w.q1 = q0 + n_pos;
   const u64 P = h->d.P, k = h->p.k;
   // Bucket capacity from the window count of reads of length >= k (exact for such reads);
-  // shorter reads, hash imbalance and repeated k-mers spill into the overflow area.
+  // shorter reads, hash imbalance and repeated k-mers spill into the overflow area. Both are
+  // multiples of 16 records (the record passes stage 16-byte aligned tiles).
   const u64 w_est = n_bases > (k - 1) * n_reads ? n_bases - (k - 1) * n_reads : 0;
-  u64 cap = (u64)((double)w_est / (double)P * 1.05) + 64;
+  u64 cap = ((u64)((double)w_est / (double)P * 1.05) + 64 + 15) & ~15ull;
   u64 ocap = n_pos / 16 + 65536;
   if (P * cap < n_bases) ocap = std::max(ocap, n_bases - P * cap + n_pos / 64);
+  ocap = (ocap + 15) & ~15ull;
   if (cap >= (1ull << 32)) return KMA_EINVAL;  // more partitions needed for this batch size
+  h->count_bound += cap + ocap;
+  const PartGeom g = part_geom(h);
   const u64 total = P * cap + ocap;
   kma_handle::RecBatch rb{nullptr, nullptr, nullptr, cap, ocap};
   const size_t kb = (size_t)total * (k > 32 ? 16 : 8);
@@ -883,6 +895,7 @@ int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uin
       part_later.push_back({h, q0, n_pos, reads[i].n_reads, reads[i].n_bases});
       continue;
     }
+    h->count_bound += n_pos;
     PassDesc d = pass_desc(h, h->p.use_bloom ? kModeBloom : kModeCount, q0, q0 + n_pos);
     d.tile_begin = tiles;
     tiles += (n_pos + tile - 1) / tile;

@@ -90,6 +90,60 @@ __device__ __forceinline__ void st_stream(unsigned char* p, unsigned v, u64 pol)
   asm volatile("st.global.L2::cache_hint.u8 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
 }
 
+
+// ------------------------------------------------------------------ bulk copies (TMA)
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// 1-D TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
+// completion signalled on the mbarrier as transaction bytes.
+__device__ __forceinline__ void tma_load_1d(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// The same copy with an L2 cache policy (evict-first for streams read once).
+__device__ __forceinline__ void tma_load_1d_hint(unsigned dst, const void* src, unsigned bytes, unsigned bar,
+                                                 u64 pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar), "l"(pol) : "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses to shared memory before later bulk
+// copies into it (a buffer read by the CTA, then refilled by a copy).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned phase) {
+  unsigned done;
+  asm volatile("{\n\t.reg .pred p;\n\t"
+               "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(done) : "r"(bar), "r"(phase) : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the mbarrier phase: returns false (and the caller raises a status flag)
+// if the copies have not completed after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned phase, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
 // ------------------------------------------------------------------ 2-bit words
 
 // Reverse the order of the 32 two-bit groups of x.
@@ -241,37 +295,62 @@ __device__ __forceinline__ const Slot* find(const Slot* table, u64 slots, u64 lo
   return nullptr;
 }
 
-__device__ __forceinline__ void add_occurrence(Slot* s, const Window& w, unsigned inc,
-                                               DevStatus* st) {
-  const unsigned old = atomicAdd(&s->count, inc);
-  if (old > 0xFFFFFFFFu - inc) atomicOr(&st->flags, kFlagOverflow);
-  if (w.lu) atomicAdd(&s->ext[w.lb], 1u);
-  if (w.ru) atomicAdd(&s->ext[4 + w.rb], 1u);
+// Counter of the occurrence's left / right outcome.
+__device__ __forceinline__ unsigned* left_counter(Slot* s, const Window& w) {
+  return w.lu ? &s->ext[w.lb] : &s->none[0];
+}
+__device__ __forceinline__ unsigned* right_counter(Slot* s, const Window& w) {
+  return w.ru ? &s->ext[4 + w.rb] : &s->none[1];
 }
 
-// Warp-aggregated variant: lanes in `act` holding the same slot merge their count into one
-// atomic, and lanes adding to the same extension counter merge theirs.
+// One occurrence (inc of them) of the slot's key, with wrap detection: every counter is at
+// most the key's count, so a wrap of either updated counter is the only way one can be lost
+// (a total count above 2^32 is caught when the counters are summed).
+__device__ __forceinline__ void add_occurrence(Slot* s, const Window& w, unsigned inc,
+                                               DevStatus* st) {
+  const unsigned a = atomicAdd(left_counter(s, w), inc);
+  const unsigned b = atomicAdd(right_counter(s, w), inc);
+  if (a > 0xFFFFFFFFu - inc || b > 0xFFFFFFFFu - inc) atomicOr(&st->flags, kFlagOverflow);
+}
+
+// Count update when no counter can reach 2^32 (the host bounds the occurrences a key can
+// have before the next reset): reductions without a returned value, nothing to wait for.
+__device__ __forceinline__ void red_add(unsigned* a, unsigned v) {
+  asm volatile("red.global.add.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void add_occurrence_red(Slot* s, const Window& w) {
+  red_add(left_counter(s, w), 1u);
+  red_add(right_counter(s, w), 1u);
+}
+
+// Warp-aggregated variant: lanes in `act` adding to the same counter merge their updates.
 __device__ __forceinline__ void add_occurrence_agg(unsigned act, Slot* s, const Window& w,
                                                    DevStatus* st) {
   const int lane = threadIdx.x & 31;
-  const unsigned peers = __match_any_sync(act, reinterpret_cast<u64>(s));
-  if (lane == __ffs(peers) - 1) {
-    const unsigned inc = __popc(peers);
-    const unsigned old = atomicAdd(&s->count, inc);
-    if (old > 0xFFFFFFFFu - inc) atomicOr(&st->flags, kFlagOverflow);
+  unsigned* l = left_counter(s, w);
+  unsigned* r = right_counter(s, w);
+  const unsigned ml = __match_any_sync(act, reinterpret_cast<u64>(l));
+  const unsigned mr = __match_any_sync(act, reinterpret_cast<u64>(r));
+  bool wrap = false;
+  if (lane == __ffs(ml) - 1) {
+    const unsigned inc = __popc(ml);
+    wrap |= atomicAdd(l, inc) > 0xFFFFFFFFu - inc;
   }
-  const unsigned lact = __ballot_sync(act, w.lu);
-  if (w.lu) {
-    unsigned* a = &s->ext[w.lb];
-    const unsigned m = __match_any_sync(lact, reinterpret_cast<u64>(a));
-    if (lane == __ffs(m) - 1) atomicAdd(a, (unsigned)__popc(m));
+  if (lane == __ffs(mr) - 1) {
+    const unsigned inc = __popc(mr);
+    wrap |= atomicAdd(r, inc) > 0xFFFFFFFFu - inc;
   }
-  const unsigned ract = __ballot_sync(act, w.ru);
-  if (w.ru) {
-    unsigned* a = &s->ext[4 + w.rb];
-    const unsigned m = __match_any_sync(ract, reinterpret_cast<u64>(a));
-    if (lane == __ffs(m) - 1) atomicAdd(a, (unsigned)__popc(m));
+  if (wrap) atomicOr(&st->flags, kFlagOverflow);
+}
+
+// Count of a slot (sum of its left outcomes), flagged if it does not fit 32 bits.
+__device__ __forceinline__ unsigned slot_count(unsigned none_l, uint4 el, DevStatus* st) {
+  const u64 c = (u64)none_l + el.x + el.y + el.z + el.w;
+  if (c > 0xFFFFFFFFull) {
+    atomicOr(&st->flags, kFlagOverflow);
+    return 0xFFFFFFFFu;
   }
+  return (unsigned)c;
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {

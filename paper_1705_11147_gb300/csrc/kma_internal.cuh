@@ -31,13 +31,16 @@ constexpr uint32_t kFlagOverflow = 2u;
 constexpr uint32_t kFlagBadOffsets = 4u;
 constexpr uint32_t kFlagTimeout = 8u;     // a bounded device wait gave up
 
-// One hash-table slot: the key and count share the first 32-byte sector, the eight
-// extension counters fill the second, so an update touches one half cache line.
+// One hash-table slot. Every occurrence has exactly one left outcome (a usable base A/C/G/T
+// or none) and one right outcome, so the slot keeps five counters per side and no separate
+// count: count = none[0] + ext[0..3] = none[1] + ext[4..7]. An occurrence costs two
+// counter updates. The key and the two "none" counters share the first 32-byte sector, the
+// eight extension counters fill the second.
 struct __align__(64) Slot {
   unsigned long long lo, hi;
-  unsigned int count;
-  unsigned int pad[3];
-  unsigned int ext[8];  // left A C G T, right A C G T
+  unsigned int none[2];  // occurrences without a usable left / right extension base
+  unsigned int pad[2];
+  unsigned int ext[8];   // left A C G T, right A C G T
 };
 static_assert(sizeof(Slot) == 64, "slot must be 64 bytes");
 
@@ -73,6 +76,8 @@ struct PassDesc {
   unsigned int mode;              // kModeBloom / kModeCount / kModeRecount
   unsigned int n_parts;           // owner-computes partition: count only keys owned by `part`
   unsigned int part;
+  unsigned int no_overflow;       // 1: no count can reach 2^32 (host bound), counts use red.add
+  unsigned int pad;
 };
 
 struct PassBatch {
@@ -162,6 +167,8 @@ struct PartGeom {
   unsigned int n_parts;         // multi-GPU owner filter (as PassDesc)
   unsigned int part;
   unsigned int rpt;             // records per thread in flight in the record passes (2 or 4)
+  unsigned int wait_limit;      // polls of the bounded wait for a staged record tile
+  unsigned int no_overflow;     // 1: no count can reach 2^32 (host bound), counts use red.add
   unsigned int pad;
 };
 
@@ -174,7 +181,10 @@ struct PartWindows {
 };
 
 // Record buckets of one count() batch: P buckets of `cap` records (bucket p starts at p*cap),
-// then an overflow area of `ocap` records for partitions whose bucket filled up. fill[p]
+// then an overflow area of `ocap` records for partitions whose bucket filled up. cap and ocap
+// are multiples of 16 and both arrays 16-byte aligned, so every tile of the record passes
+// starts on a 16-byte boundary and may be staged with 1-D bulk copies rounded up to 16
+// records without leaving its bucket (or the overflow area). fill[p]
 // counts the records that were assigned to bucket p (those beyond cap went to the overflow
 // area); fill[P] counts the overflow records.
 struct PartRecords {

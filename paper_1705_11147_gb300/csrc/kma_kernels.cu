@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(256) pass_kernel(const __grid_constant__ PassB
         const unsigned a = __ballot_sync(0xffffffffu, s != nullptr);
         if (s) add_occurrence_agg(a, s, w[j], D.status);
       } else if (s) {
-        add_occurrence(s, w[j], 1u, D.status);
+        if (D.no_overflow) add_occurrence_red(s, w[j]);
+        else add_occurrence(s, w[j], 1u, D.status);
       }
     }
   }
@@ -171,78 +172,63 @@ __device__ __forceinline__ int find_pack_sample(const PackBatch& B, u64 c) {
   return lo;
 }
 
-// Last read r with start ps_r = offsets[r] - o0 + r <= p (reads of the batch: [lo, n)).
-__device__ __forceinline__ u64 read_at(const u64* off, u64 o0, u64 n, u64 lo, u64 p) {
-  u64 hi = n;
+// Last read r with start ps_r = offsets[r] - o0 + r <= p, found by a warp: the answer lies in [lo, hi) and offsets[lo] - o0 + lo <= p;
+// each round the 32 lanes test 32 evenly spaced reads, so ~log32(hi - lo) dependent loads
+// instead of log2. Called by all lanes of a warp with the same arguments; all return it.
+__device__ __forceinline__ u64 read_at_warp(const u64* off, u64 o0, u64 lo, u64 hi, u64 p) {
+  const unsigned lane = threadIdx.x & 31;
   while (hi - lo > 1) {
-    const u64 mid = (lo + hi) >> 1;
-    if (off[mid] - o0 + mid <= p) lo = mid; else hi = mid;
+    const u64 step = (hi - lo + 31) / 32;
+    const u64 idx = lo + lane * step;
+    const bool le = idx < hi && off[idx] - o0 + idx <= p;  // a prefix of the lanes (starts increase)
+    const unsigned m = __ballot_sync(0xffffffffu, le);
+    const u64 nlo = m ? lo + (u64)(31 - __clz(m)) * step : lo;
+    hi = nlo + step < hi ? nlo + step : hi;
+    lo = nlo;
   }
   return lo;
 }
 
-// Batch-relative index of the first base at or after arena position p (clamped to n_bases).
-__device__ __forceinline__ u64 base_at_or_after(const PackDesc& D, u64 o0, u64 p) {
-  if (D.n_reads == 0) return 0;
+// Batch-relative index of the first base at or after arena position p (clamped to n_bases),
+// given the read r containing p.
+__device__ __forceinline__ u64 base_at_or_after(const PackDesc& D, u64 o0, u64 r, u64 p) {
   const u64* off = D.offsets;
-  const u64 r = read_at(off, o0, D.n_reads, 0, p);
   const u64 rs = off[r] - o0 + r;
   const u64 len = off[r + 1] - off[r];
-  u64 b = (p - rs < len) ? off[r] - o0 + (p - rs) : off[r + 1] - o0;
+  const u64 b = (p - rs < len) ? off[r] - o0 + (p - rs) : off[r + 1] - o0;
   return b < D.n_bases ? b : D.n_bases;
 }
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
+// Bit i of x moved to bit 2i of the result (the other bits zero).
+__device__ __forceinline__ u64 spread_bits(unsigned x) {
+  u64 v = x;
+  v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+  v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  v = (v | (v << 2)) & 0x3333333333333333ull;
+  v = (v | (v << 1)) & 0x5555555555555555ull;
+  return v;
 }
 
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-// 1-D TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
-// completion signalled on the mbarrier as transaction bytes.
-__device__ __forceinline__ void tma_load_1d(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned phase) {
-  unsigned done;
-  asm volatile("{\n\t.reg .pred p;\n\t"
-               "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-               "selp.u32 %0, 1, 0, p;\n\t}"
-               : "=r"(done) : "r"(bar), "r"(phase) : "memory");
-  return done != 0;
-}
-
-// Bounded wait for the mbarrier phase: returns false (and the caller raises a status flag)
-// if the copies have not completed after `limit` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned phase, unsigned limit) {
-  for (unsigned it = 0; it < limit; ++it)
-    if (mbar_try_wait(bar, phase)) return true;
-  return false;
-}
-
-constexpr int kPackThreads = 256;                     // one thread per 64 positions
+constexpr int kPackThreads = 256;                     // 8 warps, one 64-position word per thread
 constexpr int kPackChunk = kPackThreads * 64;         // positions per CTA chunk
 constexpr int kPackBuf = kPackChunk + 32;             // staged bytes (+ alignment slack)
 
 // One CTA chunk = 256 words of 64 arena positions of one sample. The bases (and qualities)
 // the chunk covers are one contiguous byte range of the input; thread 0 locates it and
-// stages it into shared memory with two 1-D TMA bulk copies; then every thread packs its 64
-// positions from shared memory into two code words, one invalid word and one hq word.
+// stages it into shared memory with two 1-D TMA bulk copies. Each warp then packs 32 words,
+// 32 consecutive positions at a time (lane l takes position l, so shared-memory reads are
+// consecutive bytes): four warp votes give the two code bits, the invalid bit and the
+// high-quality bit of the 32 positions. At the end lane j turns the votes of word j into its
+// code, complemented-code, invalid and high-quality words (bit interleaving), so the words
+// are stored coalesced.
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constant__ PackBatch B) {
   __shared__ __align__(16) unsigned char s_seq[kPackBuf];
   __shared__ __align__(16) unsigned char s_qual[kPackBuf];
   __shared__ __align__(8) unsigned long long s_bar;
-  __shared__ u64 s_b0, s_b1, s_r0;
+  __shared__ u64 s_b0, s_b1, s_r0, s_r1;
   __shared__ unsigned s_lead, s_ok;
+  __shared__ uint4 s_bal[kPackThreads / 32][64];  // per warp: votes of its 64 32-position steps
   const unsigned bar = smem_u32(&s_bar);
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
@@ -256,12 +242,32 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
     const u64 words = D.n_pos / 64;
     const u64 w0 = (c - D.chunk_begin) * kPackThreads;
     const u64 w1 = (w0 + kPackThreads < words) ? w0 + kPackThreads : words;
+    // warp 0 finds the read at the chunk's first position, warp 1 the one at its end
+    const unsigned warp = threadIdx.x >> 5;
+    if (warp < 2) {
+      const u64 p = (warp == 0 ? w0 : w1) * 64;
+      u64 r = 0, b = 0;
+      if (D.n_reads) {
+        r = read_at_warp(off, o0, 0, D.n_reads, p);
+        b = base_at_or_after(D, o0, r, p);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        if (warp == 0) {
+          s_b0 = b;
+          s_r0 = r;
+        } else {
+          s_b1 = b;
+          s_r1 = r;
+        }
+      }
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       if (w0 == 0 && off[D.n_reads] - o0 != D.n_bases) atomicOr(&D.status->flags, kFlagBadOffsets);
-      u64 b0 = base_at_or_after(D, o0, w0 * 64);
-      u64 b1 = base_at_or_after(D, o0, w1 * 64);
+      const u64 b0 = s_b0;
+      u64 b1 = s_b1;
       unsigned ok = 1;
-      if (b1 < b0 || b1 - b0 > (u64)kPackChunk) {  // only possible with inconsistent offsets
+      if (b1 < b0 || b1 - b0 > (u64)kPackChunk || s_r1 < s_r0) {  // only with inconsistent offsets
         atomicOr(&D.status->flags, kFlagBadOffsets);
         b1 = b0;
         ok = 0;
@@ -273,9 +279,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
       // stage it from its own aligned base (lead differs) -- handled by two leads below
       const unsigned leadq = (unsigned)(aq & 15);
       const unsigned n = (unsigned)(b1 - b0);
-      s_b0 = b0;
       s_b1 = b1;
-      s_r0 = D.n_reads ? read_at(off, o0, D.n_reads, 0, w0 * 64) : 0;
       s_lead = lead | (leadq << 8);
       s_ok = ok;
       if (n) {
@@ -302,50 +306,62 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
     }
     __syncthreads();
     if (s_ok == 2) return;  // uniform: the chunk's input never arrived
-    const u64 b0 = s_b0, b1 = s_b1;
+    const unsigned nb = (unsigned)(s_b1 - s_b0);  // staged bases
     const unsigned lead = s_lead & 0xFF, leadq = s_lead >> 8;
-    const u64 w = w0 + threadIdx.x;
-    if (w < w1 && s_ok) {
-      const u64 p0 = w * 64;
-      u64 r = D.n_reads ? read_at(off, o0, D.n_reads, s_r0, p0) : 0;
-      u64 rs = D.n_reads ? off[r] - o0 + r : 0;
-      u64 re = D.n_reads ? off[r + 1] - o0 + r : 0;
-      u64 c0 = 0, c1 = 0, r0 = 0, r1 = 0, inv = 0, hq = 0;
+    const unsigned lane = threadIdx.x & 31;
+    const u64 ww0 = w0 + warp * 32;                  // first word of this warp
+    const u64 gw = (D.q0 >> 6) + w0 + threadIdx.x;  // the word this lane stores
+    if (ww0 < w1 && s_ok) {
+      // Positions are handled relative to the chunk start P0 (32-bit). A base of read r at
+      // position p has batch base index p - r; the chunk's staged bytes start at the base of
+      // the chunk's first position, so its byte offset is (p - P0) - (r - r0).
+      const u64 nr = D.n_reads, P0 = w0 * 64, r0 = s_r0;
+      u64 r = nr ? read_at_warp(off, o0, s_r0, s_r1 + 1, ww0 * 64) : 0;
+      // first position of read r + 1, relative to P0 (saturated: beyond the chunk)
+      auto next_start = [&](u64 rr) -> unsigned {
+        if (rr >= nr) return 0xFFFFFFFFu;
+        const u64 sn = off[rr + 1] - o0 + rr + 1 - P0;
+        return sn < 0xFFFFFFFFull ? (unsigned)sn : 0xFFFFFFFFu;
+      };
+      unsigned snext = next_start(r);
+      unsigned rd = (unsigned)(r - r0);  // read index relative to the chunk's first read
+      const unsigned nrd = (unsigned)(nr - r0);
+      uint4* bal = s_bal[warp];
 #pragma unroll 4
-      for (int i = 0; i < 64; ++i) {
-        const u64 p = p0 + i;
-        while (r < D.n_reads && p > re) {  // move to the read containing p
-          ++r;
-          if (r < D.n_reads) {
-            rs = off[r] - o0 + r;
-            re = off[r + 1] - o0 + r;
-          }
+      for (unsigned it = 0; it < 64; ++it) {
+        const unsigned pr = warp * 2048u + it * 32u + lane;
+        while (rd < nrd && pr >= snext) {  // the lane's read (reads may be shorter than 32)
+          ++rd;
+          snext = next_start(r0 + rd);
         }
         unsigned code = 0, valid = 0, good = 0;
-        const u64 bidx = off[r] - o0 + (p - rs);
-        if (r < D.n_reads && p < re && p >= rs && bidx >= b0 && bidx < b1) {
-          const unsigned ch = s_seq[lead + (unsigned)(bidx - b0)] & 0xDFu;
-          valid = (ch == 'A') | (ch == 'C') | (ch == 'G') | (ch == 'T');
-          code = ch == 'C' ? 1u : ch == 'G' ? 2u : ch == 'T' ? 3u : 0u;
-          good = valid && (unsigned)s_qual[leadq + (unsigned)(bidx - b0)] >= D.qual_min;
+        const unsigned bi = pr - rd;  // staged byte of this position, if it is a base
+        if (rd < nrd && pr + 1u != snext && bi < nb) {
+          const unsigned ch = s_seq[lead + bi];
+          const unsigned u = (ch & 0xDFu) - 0x40u;  // A C G T (either case) -> bits 1 3 7 20
+          valid = u < 32u ? (0x10008Au >> u) & 1u : 0u;
+          code = valid ? ((ch >> 1) ^ (ch >> 2)) & 3u : 0u;  // A0 C1 G2 T3
+          good = valid && (unsigned)s_qual[leadq + bi] >= D.qual_min;
         }
-        if (i < 32) {
-          c0 |= (u64)code << (62 - 2 * i);
-          r0 |= (u64)(3u - code) << (2 * i);
-        } else {
-          c1 |= (u64)code << (62 - 2 * (i - 32));
-          r1 |= (u64)(3u - code) << (2 * (i - 32));
-        }
-        inv |= (u64)(!valid) << (63 - i);
-        hq |= (u64)good << (63 - i);
+        const unsigned m1 = __ballot_sync(0xffffffffu, code >> 1);
+        const unsigned m0 = __ballot_sync(0xffffffffu, code & 1u);
+        const unsigned mi = __ballot_sync(0xffffffffu, !valid);
+        const unsigned mh = __ballot_sync(0xffffffffu, good);
+        if (lane == 0) bal[it] = make_uint4(m1, m0, mi, mh);
       }
-      const u64 gw = (D.q0 >> 6) + w;
-      reinterpret_cast<ulonglong2*>(D.codes)[gw] = make_ulonglong2(c0, c1);
-      reinterpret_cast<ulonglong2*>(D.rcodes)[gw] = make_ulonglong2(r0, r1);
-      D.inv[gw] = inv;
-      D.hq[gw] = hq;
-    } else if (w < w1) {
-      const u64 gw = (D.q0 >> 6) + w;
+      __syncwarp();
+      if (w0 + threadIdx.x < w1) {  // lane j assembles word j from its two 32-position halves
+        const uint4 a = bal[2 * lane], b = bal[2 * lane + 1];
+        const u64 c0 = (spread_bits(__brev(a.x)) << 1) | spread_bits(__brev(a.y));
+        const u64 c1 = (spread_bits(__brev(b.x)) << 1) | spread_bits(__brev(b.y));
+        const u64 q0 = (spread_bits(~a.x) << 1) | spread_bits(~a.y);
+        const u64 q1 = (spread_bits(~b.x) << 1) | spread_bits(~b.y);
+        reinterpret_cast<ulonglong2*>(D.codes)[gw] = make_ulonglong2(c0, c1);
+        reinterpret_cast<ulonglong2*>(D.rcodes)[gw] = make_ulonglong2(q0, q1);
+        D.inv[gw] = ((u64)__brev(a.z) << 32) | __brev(b.z);
+        D.hq[gw] = ((u64)__brev(a.w) << 32) | __brev(b.w);
+      }
+    } else if (w0 + threadIdx.x < w1) {
       reinterpret_cast<ulonglong2*>(D.codes)[gw] = make_ulonglong2(0, 0);
       reinterpret_cast<ulonglong2*>(D.rcodes)[gw] = make_ulonglong2(~0ull, ~0ull);
       D.inv[gw] = ~0ull;
@@ -392,7 +408,11 @@ __global__ void __launch_bounds__(kClassThreads) classify_kernel(const __grid_co
       keep[it] = false;
       if (i < D.slots) {
         const Slot* s = D.table + i;
-        if (__ldcg(&s->hi) != kEmpty && __ldcg(&s->count) >= D.min_depth) keep[it] = true;
+        if (__ldcg(&s->hi) != kEmpty) {  // count = left outcomes (none + A C G T)
+          const uint4 el = __ldcg(reinterpret_cast<const uint4*>(&s->ext[0]));
+          const u64 c = (u64)__ldcg(&s->none[0]) + el.x + el.y + el.z + el.w;
+          keep[it] = c >= D.min_depth;
+        }
       }
       nk += keep[it];
     }
@@ -419,9 +439,9 @@ __global__ void __launch_bounds__(kClassThreads) classify_kernel(const __grid_co
       const u64 i = first + (u64)it * kClassThreads + threadIdx.x;
       const Slot* s = D.table + i;
       const ulonglong2 kv = __ldcg(reinterpret_cast<const ulonglong2*>(s));
-      const unsigned c = __ldcg(&s->count);
       const uint4 e0 = __ldcg(reinterpret_cast<const uint4*>(&s->ext[0]));
       const uint4 e1 = __ldcg(reinterpret_cast<const uint4*>(&s->ext[4]));
+      const unsigned c = slot_count(__ldcg(&s->none[0]), e0, D.status);
       const unsigned el[4] = {e0.x, e0.y, e0.z, e0.w};
       const unsigned er[4] = {e1.x, e1.y, e1.z, e1.w};
       const unsigned lc = side_code(el, D.min_ext), rc = side_code(er, D.min_ext);
@@ -474,8 +494,9 @@ __global__ void __launch_bounds__(256) query_kernel(const Slot* table, u64 slots
       const Slot* sub = parts > 1 ? table + (u64)part_of(h, parts) * slots : table;
       const Slot* s = find(sub, slots, lo, hi, h, full);
       if (full) atomicOr(&st->flags, kFlagFull);
-      if (s && s->count >= min_depth) {
-        c = s->count;
+      const unsigned sc = s ? slot_count(s->none[0], *reinterpret_cast<const uint4*>(&s->ext[0]), st) : 0u;
+      if (s && sc >= min_depth) {
+        c = sc;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           if (forward) {
@@ -554,7 +575,12 @@ cudaError_t launch_pass(const PassBatch& b, const LaunchShape& shape, bool agg, 
 cudaError_t launch_pack(const PackBatch& b, cudaStream_t stream, int num_sms) {
   if (b.total_chunks == 0) return cudaSuccess;
   u64 blocks = b.total_chunks;
-  const u64 cap = (u64)num_sms * 4;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel, kPackThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 4;
+  }
+  const u64 cap = (u64)num_sms * (per_sm > 0 ? per_sm : 1);
   if (blocks > cap) blocks = cap;
   pack_kernel<<<(unsigned)blocks, kPackThreads, 0, stream>>>(b);
   return cudaGetLastError();

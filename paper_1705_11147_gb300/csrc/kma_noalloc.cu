@@ -160,6 +160,7 @@ extern "C" int kmer_analysis_count_small_noalloc(const kma_params* params, const
     d.canonical = p.canonical;
     d.mode = kModeCount;  // every window straight into the table: no Bloom filter to hold
     d.n_parts = 1;
+    d.no_overflow = 1;    // at most n_pos < 2^32 occurrences per key
     LaunchShape shape{256, 2, num_sms * 2};
     b.total_tiles = (n_pos + 511) / 512;
     if ((rc = check(launch_pass(b, shape, false, stream)))) return rc;

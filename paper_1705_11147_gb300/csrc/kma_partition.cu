@@ -183,73 +183,172 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const __grid
 // ------------------------------------------------------------------ record pass
 //
 // Tiles walk the buckets in partition order (then the overflow area), so at any moment the
-// CTAs work on one or two partitions whose sub-filter and sub-table sit in L2.
+// CTAs work on one or two partitions whose sub-filter and sub-table sit in L2. Every warp
+// works on its own tiles of 32 * RPT records, staged in shared memory with 1-D bulk copies
+// and double-buffered: while the lanes resolve the atomics of one tile, the warp's next tile
+// is on its way. Warps never wait for each other (no block barriers), so a warp whose
+// probes take long does not hold up the others.
 
+template <int KW, int RPT>
+struct WarpStage {
+  static constexpr int kTile = 32 * RPT;  // a multiple of 16
+  u64 keys[2][kTile * KW];
+  unsigned char info[2][kTile];
+  unsigned char list[kTile];              // recount: indices of the flagged records
+  unsigned long long bar[2];
+};
+static_assert(sizeof(WarpStage<1, 2>) % 16 == 0 && sizeof(WarpStage<2, 2>) % 16 == 0 &&
+                  sizeof(WarpStage<1, 4>) % 16 == 0 && sizeof(WarpStage<2, 4>) % 16 == 0,
+              "every warp's staging buffers must start on a 16-byte boundary");
 
-template <int KW, int kRecPerThread>
+// Record range [base, end) of tile t, clipped to one tile; false if the tile is empty.
+template <int TILE>
+__device__ __forceinline__ bool rec_tile(const PartGeom& G, const PartRecords& R, u64 tpb, u64 t, u64& base,
+                                         u64& end) {
+  u64 f, lo, b0;
+  if (t < (u64)G.P * tpb) {
+    const u64 b = t / tpb;
+    f = R.fill[b] < R.cap ? R.fill[b] : R.cap;
+    lo = (t - b * tpb) * TILE;
+    b0 = b * R.cap;
+  } else {
+    f = R.fill[G.P] < R.ocap ? R.fill[G.P] : R.ocap;
+    lo = (t - (u64)G.P * tpb) * TILE;
+    b0 = (u64)G.P * R.cap;
+  }
+  if (lo >= f) return false;
+  base = b0 + lo;
+  end = b0 + (f - lo < (u64)TILE ? f : lo + TILE);
+  return true;
+}
+
+// First non-empty tile at or after t in steps of `step` (n_tiles if none).
+template <int TILE>
+__device__ __forceinline__ u64 rec_next(const PartGeom& G, const PartRecords& R, u64 tpb, u64 n_tiles, u64 t,
+                                        u64 step, u64& base, u64& end) {
+  base = end = 0;
+  while (t < n_tiles && !rec_tile<TILE>(G, R, tpb, t, base, end)) t += step;
+  return t;
+}
+
+// Lane 0: stage the records [base, end) into buffer `buf` (sizes rounded up to 16 records,
+// which stays inside the bucket because cap and ocap are multiples of 16).
+template <int KW, int RPT>
+__device__ __forceinline__ void rec_issue(WarpStage<KW, RPT>& S, const PartRecords& R, int buf, u64 base, u64 end,
+                                          u64 pol) {
+  const unsigned n16 = (unsigned)((end - base + 15) & ~15ull);
+  const unsigned kb = n16 * 8u * KW;
+  const unsigned bar = smem_u32(&S.bar[buf]);
+  fence_proxy_async_smem();
+  mbar_expect_tx(bar, kb + n16);
+  tma_load_1d_hint(smem_u32(S.keys[buf]), reinterpret_cast<const u64*>(R.keys) + base * KW, kb, bar, pol);
+  tma_load_1d_hint(smem_u32(S.info[buf]), R.info + base, n16, bar, pol);
+}
+
+__device__ __forceinline__ u64 shfl0(u64 v) { return __shfl_sync(0xffffffffu, v, 0); }
+
+template <int KW, int RPT, unsigned MODE>
 __global__ void __launch_bounds__(kPartThreads) part_pass_kernel(const __grid_constant__ PartGeom G,
-                                                                 const __grid_constant__ PartRecords R,
-                                                                 unsigned mode) {
-  constexpr int kRecTile = kPartThreads * kRecPerThread;
-  const unsigned lane = threadIdx.x & 31;
-  const u64 tpb = (R.cap + kRecTile - 1) / kRecTile;          // tiles per bucket
-  const u64 otiles = (R.ocap + kRecTile - 1) / kRecTile;
-  const u64 n_tiles = (u64)G.P * tpb + otiles;
-  u64 acc_ins = 0, acc_first = 0;
+                                                                 const __grid_constant__ PartRecords R) {
+  constexpr int kTile = WarpStage<KW, RPT>::kTile;
+  constexpr int kWarps = kPartThreads / 32;
+  __shared__ __align__(128) WarpStage<KW, RPT> stage[kWarps];
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpStage<KW, RPT>& S = stage[warp];
+  const u64 step = (u64)gridDim.x * kWarps;
+  const u64 tpb = (R.cap + kTile - 1) / kTile;  // tiles per bucket
+  const u64 ofill = R.fill[G.P] < R.ocap ? R.fill[G.P] : R.ocap;
+  const u64 n_tiles = (u64)G.P * tpb + (ofill + kTile - 1) / kTile;
   const u64 pol = policy_evict_first();
-  for (u64 t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    // record range of this tile
-    u64 base, end;
-    if (t < (u64)G.P * tpb) {
-      const u64 b = t / tpb;
-      const u64 f = R.fill[b] < R.cap ? R.fill[b] : R.cap;
-      const u64 lo = (t - b * tpb) * kRecTile;
-      if (lo >= f) continue;  // tile-uniform
-      base = b * R.cap + lo;
-      end = b * R.cap + f;
-    } else {
-      const u64 f = R.fill[G.P] < R.ocap ? R.fill[G.P] : R.ocap;
-      const u64 lo = (t - (u64)G.P * tpb) * kRecTile;
-      if (lo >= f) continue;
-      base = (u64)G.P * R.cap + lo;
-      end = (u64)G.P * R.cap + f;
+  u64 acc_ins = 0, acc_first = 0;
+  unsigned phases = 0;  // bit b: parity to wait for on buffer b (same in every lane)
+
+  u64 t, base, end;
+  if (lane == 0) {
+    mbar_init(smem_u32(&S.bar[0]), 1);
+    mbar_init(smem_u32(&S.bar[1]), 1);
+    t = rec_next<kTile>(G, R, tpb, n_tiles, (u64)blockIdx.x * kWarps + warp, step, base, end);
+    if (t < n_tiles) rec_issue(S, R, 0, base, end, pol);
+  }
+  __syncwarp();  // barriers initialised before any lane polls them
+  t = shfl0(t);
+  base = shfl0(base);
+  end = shfl0(end);
+  int buf = 0;
+  while (t < n_tiles) {
+    // prefetch the warp's next non-empty tile into the other buffer, then wait for this one
+    u64 tn, nb, ne;
+    if (lane == 0) {
+      tn = rec_next<kTile>(G, R, tpb, n_tiles, t + step, step, nb, ne);
+      if (tn < n_tiles) rec_issue(S, R, buf ^ 1, nb, ne, pol);
     }
-    Window w[kRecPerThread];
-    u64 h[kRecPerThread], idx[kRecPerThread];
-    unsigned p[kRecPerThread];
-    unsigned char inf[kRecPerThread];
-    bool act[kRecPerThread];
-    // stage 1: records (coalesced, streamed)
+    tn = shfl0(tn);
+    nb = shfl0(nb);
+    ne = shfl0(ne);
+    const unsigned bar = smem_u32(&S.bar[buf]);
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, (phases >> buf) & 1u, G.wait_limit));
+    if (!ok) {  // give up: report, let the copies in flight land (bounded), stop the warp
+      if (lane == 0) {
+        atomicOr(&G.status->flags, kFlagTimeout);
+        mbar_wait_bounded(bar, (phases >> buf) & 1u, G.wait_limit);
+        if (tn < n_tiles) mbar_wait_bounded(smem_u32(&S.bar[buf ^ 1]), (phases >> (buf ^ 1)) & 1u, G.wait_limit);
+      }
+      return;
+    }
+    phases ^= 1u << buf;
+    const unsigned n = (unsigned)(end - base);
+    const u64* sk = S.keys[buf];
+    const unsigned char* si = S.info[buf];
+
+    // records of this tile the lanes work on: all of them, or (recount) the flagged ones,
+    // compacted so that every lane has work
+    unsigned nwork = n;
+    if (MODE == kModeRecount) {
+      unsigned below = 0;
 #pragma unroll
-    for (int j = 0; j < kRecPerThread; ++j) {
-      const u64 i = base + (u64)j * blockDim.x + threadIdx.x;
-      act[j] = i < end;
+      for (int j = 0; j < RPT; ++j) {
+        const unsigned i = j * 32 + lane;
+        const bool f = i < n && (si[i] & kInfoFirst);
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (f) S.list[below + __popc(m & ((1u << lane) - 1u))] = (unsigned char)i;
+        below += __popc(m);
+      }
+      nwork = below;
+      __syncwarp();
+    }
+
+    Window w[RPT];
+    u64 h[RPT];
+    unsigned p[RPT], rec[RPT];
+    bool act[RPT];
+    // stage 1: records from shared memory
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+      const unsigned k = j * 32 + lane;
+      act[j] = k < nwork;
+      rec[j] = MODE == kModeRecount ? (act[j] ? S.list[k] : 0u) : k;
       h[j] = 0;
       p[j] = 0;
-      inf[j] = 0;
       if (act[j]) {
-        inf[j] = (unsigned char)ld_stream(R.info + i, pol);
-        if (mode == kModeRecount && !(inf[j] & kInfoFirst)) act[j] = false;  // keys not needed
-      }
-      if (act[j]) {
+        const unsigned i = rec[j];
         if (KW == 1) {
-          w[j].lo = ld_stream(reinterpret_cast<const u64*>(R.keys) + i, pol);
+          w[j].lo = sk[i];
           w[j].hi = 0;
         } else {
-          const ulonglong2 kk = ld_stream(reinterpret_cast<const ulonglong2*>(R.keys) + i, pol);
+          const ulonglong2 kk = reinterpret_cast<const ulonglong2*>(sk)[i];
           w[j].lo = kk.x;
           w[j].hi = kk.y;
         }
-        window_of(inf[j], w[j]);
+        window_of(si[i], w[j]);
         h[j] = key_hash(w[j].lo, w[j].hi);
         p[j] = part_of(h[j], G.P);
       }
     }
-    // stage 2: Bloom test-and-set in the partition's sub-filter
-    if (mode == kModeBloom) {
-      u64 old[kRecPerThread], msk[kRecPerThread];
+    // stage 2: Bloom test-and-set in the partition's sub-filter; first sightings flagged
+    if (MODE == kModeBloom) {
+      u64 old[RPT], msk[RPT];
 #pragma unroll
-      for (int j = 0; j < kRecPerThread; ++j) {
+      for (int j = 0; j < RPT; ++j) {
         old[j] = msk[j] = 0;
         if (act[j]) {
           msk[j] = bloom_mask(h[j], G.bloom_h);
@@ -257,17 +356,18 @@ __global__ void __launch_bounds__(kPartThreads) part_pass_kernel(const __grid_co
         }
       }
 #pragma unroll
-      for (int j = 0; j < kRecPerThread; ++j) {
+      for (int j = 0; j < RPT; ++j) {
         const bool first = act[j] && (old[j] & msk[j]) != msk[j];
-        if (first) st_stream(R.info + base + (u64)j * blockDim.x + threadIdx.x, inf[j] | kInfoFirst, pol);
+        if (first) st_stream(R.info + base + rec[j], (unsigned)si[rec[j]] | kInfoFirst, pol);
         acc_first += __popc(__ballot_sync(0xffffffffu, first));
         act[j] = act[j] && !first;
       }
     }
     // stage 3: first probe in the partition's sub-table
-    ulonglong2 kv[kRecPerThread];
+    ulonglong2 kv[RPT];
+    u64 idx[RPT];
 #pragma unroll
-    for (int j = 0; j < kRecPerThread; ++j) {
+    for (int j = 0; j < RPT; ++j) {
       kv[j] = make_ulonglong2(0, 0);
       idx[j] = 0;
       if (act[j]) {
@@ -277,12 +377,12 @@ __global__ void __launch_bounds__(kPartThreads) part_pass_kernel(const __grid_co
     }
     // stage 4: resolve and count
 #pragma unroll
-    for (int j = 0; j < kRecPerThread; ++j) {
+    for (int j = 0; j < RPT; ++j) {
       Slot* s = nullptr;
       bool inserted = false;
       if (act[j]) {
         Slot* sub = G.table + (u64)p[j] * G.Sp;
-        if (mode == kModeRecount) {
+        if (MODE == kModeRecount) {
           bool full;
           s = resolve_find(sub, G.Sp, idx[j], kv[j], w[j].lo, w[j].hi, full);
           if (full) atomicOr(&G.status->flags, kFlagFull);
@@ -291,9 +391,17 @@ __global__ void __launch_bounds__(kPartThreads) part_pass_kernel(const __grid_co
           if (!s) atomicOr(&G.status->flags, kFlagFull);
         }
       }
-      acc_ins += __popc(__ballot_sync(0xffffffffu, inserted));
-      if (s) add_occurrence(s, w[j], 1u, G.status);
+      if (MODE != kModeRecount) acc_ins += __popc(__ballot_sync(0xffffffffu, inserted));
+      if (s) {
+        if (G.no_overflow) add_occurrence_red(s, w[j]);
+        else add_occurrence(s, w[j], 1u, G.status);
+      }
     }
+    __syncwarp();  // buffer `buf` (and the list) are free for the next copy
+    t = tn;
+    base = nb;
+    end = ne;
+    buf ^= 1;
   }
   if (lane == 0) {
     if (acc_ins) atomicAdd(&G.status->table_keys, acc_ins);
@@ -328,25 +436,35 @@ cudaError_t launch_part_scatter(const PartGeom& g, const PartWindows& w, const P
   return cudaGetLastError();
 }
 
-template <int KW, int RPT>
-static cudaError_t launch_pass_rt(const PartGeom& g, const PartRecords& r, unsigned mode, cudaStream_t stream,
-                                  int num_sms) {
-  constexpr int tile = kPartThreads * RPT;
+template <int KW, int RPT, unsigned MODE>
+static cudaError_t launch_pass_rt(const PartGeom& g, const PartRecords& r, cudaStream_t stream, int num_sms) {
+  constexpr int tile = 32 * RPT;
   const u64 tiles = (u64)g.P * ((r.cap + tile - 1) / tile) + (r.ocap + tile - 1) / tile;
   if (tiles == 0) return cudaSuccess;
-  u64 grid = grid_for((const void*)part_pass_kernel<KW, RPT>, kPartThreads, 0, num_sms);
+  if ((r.cap | r.ocap) & 15 || (reinterpret_cast<uintptr_t>(r.keys) | reinterpret_cast<uintptr_t>(r.info)) & 15)
+    return cudaErrorInvalidValue;  // staging needs 16-record buckets on 16-byte boundaries
+  const void* fn = (const void*)part_pass_kernel<KW, RPT, MODE>;
+  u64 grid = grid_for(fn, kPartThreads, 0, num_sms);
   if (grid > tiles) grid = tiles;
-  part_pass_kernel<KW, RPT><<<(unsigned)grid, kPartThreads, 0, stream>>>(g, r, mode);
+  part_pass_kernel<KW, RPT, MODE><<<(unsigned)grid, kPartThreads, 0, stream>>>(g, r);
   return cudaGetLastError();
+}
+
+template <int KW, int RPT>
+static cudaError_t launch_pass_mode(const PartGeom& g, const PartRecords& r, unsigned mode, cudaStream_t stream,
+                                    int num_sms) {
+  if (mode == kModeBloom) return launch_pass_rt<KW, RPT, kModeBloom>(g, r, stream, num_sms);
+  if (mode == kModeCount) return launch_pass_rt<KW, RPT, kModeCount>(g, r, stream, num_sms);
+  return launch_pass_rt<KW, RPT, kModeRecount>(g, r, stream, num_sms);
 }
 
 cudaError_t launch_part_pass(const PartGeom& g, const PartRecords& r, unsigned mode, cudaStream_t stream,
                              int num_sms) {
   if (g.rpt >= 4)
-    return g.k > 32 ? launch_pass_rt<2, 4>(g, r, mode, stream, num_sms)
-                    : launch_pass_rt<1, 4>(g, r, mode, stream, num_sms);
-  return g.k > 32 ? launch_pass_rt<2, 2>(g, r, mode, stream, num_sms)
-                  : launch_pass_rt<1, 2>(g, r, mode, stream, num_sms);
+    return g.k > 32 ? launch_pass_mode<2, 4>(g, r, mode, stream, num_sms)
+                    : launch_pass_mode<1, 4>(g, r, mode, stream, num_sms);
+  return g.k > 32 ? launch_pass_mode<2, 2>(g, r, mode, stream, num_sms)
+                  : launch_pass_mode<1, 2>(g, r, mode, stream, num_sms);
 }
 
 }  // namespace kma
