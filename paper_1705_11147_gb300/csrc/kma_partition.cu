@@ -26,29 +26,23 @@ __device__ __forceinline__ void window_of(unsigned char inf, Window& w) {
   w.ru = (inf >> 5) & 1u;
 }
 
-// Window at q of the batch, canonical key hashed, owner filter applied.
-__device__ __forceinline__ bool part_window(const PartGeom& G, const PartWindows& W, u64 q,
-                                            Window& w, u64& h) {
-  if (!load_window(W.codes, W.rcodes, W.inv, W.hq, G.k, G.canonical, q, w)) return false;
-  h = key_hash(w.lo, w.hi);
-  if (G.n_parts > 1 && owner_of(h, G.n_parts) != G.part) return false;
-  return true;
-}
-
 constexpr int kPartThreads = 256;
 
 // ------------------------------------------------------------------ scatter
 //
-// One tile = kPartThreads * kScatterWpt consecutive window starts.
-//  1. extract the windows, stage key + info in shared memory, rank each window inside its
-//     partition for this tile (shared-memory atomics);
+// One tile = kScatterThreads * kScatterWpt consecutive window starts; thread t takes the
+// kScatterWpt consecutive starts t * kScatterWpt + j.
+//  1. extract the windows (one set of word loads per thread, then the forward k-mer and its
+//     reverse complement are rolled one base at a time), stage key + info in shared memory,
+//     rank each window inside its partition for this tile (shared-memory atomics);
 //  2. exclusive scan of the per-partition counts (the tile's records sorted by partition) and
 //     one global reservation per partition present (bucket part, overflow part);
 //  3. permute the staged records into partition order and write them out: consecutive
 //     threads write consecutive records of the same bucket, so the stores coalesce.
 
-constexpr int kScatterWpt = 16;
-constexpr int kScatterTile = kPartThreads * kScatterWpt;  // 4096 (< 2^13: ranks and slots fit)
+constexpr int kScatterThreads = 512;
+constexpr int kScatterWpt = 8;
+constexpr int kScatterTile = kScatterThreads * kScatterWpt;  // 4096 (< 2^13: ranks and slots fit)
 
 __host__ __device__ constexpr size_t scatter_smem(unsigned P, int kw) {
   return (size_t)kScatterTile * (kw * 8) +   // staged keys
@@ -58,10 +52,102 @@ __host__ __device__ constexpr size_t scatter_smem(unsigned P, int kw) {
          256;                                // warp sums, tile total, alignment
 }
 
+// kScatterWpt consecutive windows starting at q (a multiple of 8), one at a time: the state
+// holds the forward k-mer F and its reverse complement R of the current window, the next
+// bases to enter (MSB first), and the invalid / high-quality bits around the windows.
+struct RollingWindows {
+  u64 fhi, flo, rhi, rlo;  // F and R as 2k-bit numbers (first base most / least significant)
+  u64 nxt;                 // bases q + k, q + k + 1, ... (MSB first)
+  u64 iv0, iv1;            // invalid bits from q (MSB first), 128 of them
+  u64 hl, hr;              // hq bits from q - 1 (left extensions) and from q + k (right)
+  unsigned left;           // base at q - 1 (left extension of window q)
+  unsigned k;
+
+  __device__ __forceinline__ void init(const PartWindows& W, unsigned kk, u64 q) {
+    k = kk;
+    const u64 v = q >> 6;
+    const unsigned t = (unsigned)(q & 63);
+    const u64 i0 = W.inv[v], i1 = W.inv[v + 1], i2 = W.inv[v + 2];
+    iv0 = fshl(i0, i1, t);
+    iv1 = fshl(i1, i2, t);
+    const u64 h0 = W.hq[v];
+    if (q > 0) {
+      const u64 vl = (q - 1) >> 6;
+      hl = fshl(W.hq[vl], W.hq[vl + 1], (unsigned)((q - 1) & 63));
+      left = code_at(W.codes, q - 1);
+    } else {
+      hl = h0 >> 1;  // no position before the arena: unusable
+      left = 0;
+    }
+    const u64 qr = q + k, vr = qr >> 6;
+    hr = fshl(W.hq[vr], W.hq[vr + 1], (unsigned)(qr & 63));
+    const u64 wr = qr >> 5;
+    nxt = fshl(W.codes[wr], W.codes[wr + 1], 2 * (unsigned)(qr & 31));
+    // window q itself, as in load_window
+    const u64 wi = q >> 5;
+    const unsigned sh2 = 2 * (unsigned)(q & 31);
+    const u64 a = W.codes[wi], b = W.codes[wi + 1];
+    const u64 top = fshl(a, b, sh2);
+    const u64 r0 = W.rcodes[wi], r1 = W.rcodes[wi + 1];
+    const u64 bot = fshr(r0, r1, sh2);
+    if (k > 32) {
+      const u64 mid = fshl(b, W.codes[wi + 2], sh2);
+      const unsigned sh = 128 - 2 * k;
+      flo = (mid >> sh) | (top << (64 - sh));
+      fhi = top >> sh;
+      rlo = bot;
+      rhi = fshr(r1, W.rcodes[wi + 2], sh2) & ((1ull << (2 * k - 64)) - 1);
+    } else {
+      flo = top >> (64 - 2 * k);
+      fhi = 0;
+      rlo = k == 32 ? bot : bot & ((1ull << (2 * k)) - 1);
+      rhi = 0;
+    }
+  }
+
+  // Window j of the run (the state holds window j): valid flag and the canonical window.
+  __device__ __forceinline__ bool get(unsigned j, unsigned canonical, Window& w) const {
+    const u64 bad = (j ? (iv0 << j) | (iv1 >> (64 - j)) : iv0) >> (64 - k);
+    if (bad) return false;
+    const unsigned ab = (unsigned)(nxt >> 62);              // base q + j + k
+    const bool au = (hr >> (63 - j)) & 1u;
+    const bool bu = (hl >> (63 - j)) & 1u;                 // base q + j - 1
+    const bool forward = !canonical || (fhi < rhi) || (fhi == rhi && flo <= rlo);
+    if (forward) {
+      w.lo = flo; w.hi = fhi;
+      w.lb = left; w.lu = bu;
+      w.rb = ab; w.ru = au;
+    } else {
+      w.lo = rlo; w.hi = rhi;
+      w.lb = 3u - ab; w.lu = au;
+      w.rb = 3u - left; w.ru = bu;
+    }
+    return true;
+  }
+
+  // Move to the next window: the base at q + j + k enters, the first base leaves.
+  __device__ __forceinline__ void roll() {
+    const unsigned b = (unsigned)(nxt >> 62);
+    nxt <<= 2;
+    if (k > 32) {
+      left = (unsigned)(fhi >> (2 * k - 66)) & 3u;
+      fhi = ((fhi << 2) | (flo >> 62)) & ((1ull << (2 * k - 64)) - 1);
+      flo = (flo << 2) | b;
+      rlo = (rlo >> 2) | (rhi << 62);
+      rhi = (rhi >> 2) | ((u64)(3u - b) << (2 * k - 66));
+    } else {
+      left = (unsigned)(flo >> (2 * k - 2)) & 3u;
+      flo = ((flo << 2) | b) & (k == 32 ? ~0ull : ((1ull << (2 * k)) - 1));
+      rlo = (rlo >> 2) | ((u64)(3u - b) << (2 * k - 2));
+    }
+  }
+};
+
 template <int KW>
-__global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const __grid_constant__ PartGeom G,
-                                                                    const __grid_constant__ PartWindows W,
-                                                                    const __grid_constant__ PartRecords R) {
+__global__ void __launch_bounds__(kScatterThreads) part_scatter_kernel(const __grid_constant__ PartGeom G,
+                                                                       const __grid_constant__ PartWindows W,
+                                                                       const __grid_constant__ PartRecords R) {
+  constexpr int kWarps = kScatterThreads / 32;
   extern __shared__ __align__(16) unsigned char s_raw[];
   const unsigned P = G.P;
   u64* s_keys = reinterpret_cast<u64*>(s_raw);                                   // [tile * KW]
@@ -71,37 +157,44 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const __grid
   unsigned* s_cnt = s_order + kScatterTile;                                      // [P]
   unsigned* s_off = s_cnt + P;                                                   // [P]
   unsigned* s_n1 = s_off + P;                                                    // [P]
-  unsigned* s_wsum = s_n1 + P;                                                   // [8 + 1]
-  unsigned char* s_info = reinterpret_cast<unsigned char*>(s_wsum + 16);         // [tile]
+  unsigned* s_wsum = s_n1 + P;                                                   // [kWarps + 1]
+  unsigned char* s_info = reinterpret_cast<unsigned char*>(s_wsum + 32);         // [tile]
   const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u64 n_tiles = (W.q1 - W.q0 + kScatterTile - 1) / kScatterTile;
   const u64 pol = policy_evict_first();
-  u64 acc_valid = 0;
+  unsigned acc_valid = 0;
   for (unsigned p = threadIdx.x; p < P; p += blockDim.x) s_cnt[p] = 0;
   __syncthreads();
   for (u64 t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     // 1: windows -> staged records, rank inside the partition
     unsigned pr[kScatterWpt];  // partition << 13 | rank, or ~0u
 #pragma unroll
-    for (int j = 0; j < kScatterWpt; ++j) {
-      const unsigned slot = j * kPartThreads + threadIdx.x;
-      const u64 q = W.q0 + t * kScatterTile + slot;
-      pr[j] = 0xFFFFFFFFu;
-      Window w;
-      u64 h = 0;
-      const bool ok = (q - lane) < W.q1 && q < W.q1 && part_window(G, W, q, w, h);
-      acc_valid += __popc(__ballot_sync(0xffffffffu, ok));
-      if (ok) {
-        const unsigned p = part_of(h, P);
-        pr[j] = (p << 13) | atomicAdd(&s_cnt[p], 1u);
-        s_keys[(size_t)slot * KW] = w.lo;
-        if (KW == 2) s_keys[(size_t)slot * KW + 1] = w.hi;
-        s_info[slot] = info_of(w);
+    for (int j = 0; j < kScatterWpt; ++j) pr[j] = 0xFFFFFFFFu;
+    const u64 q = W.q0 + t * kScatterTile + (u64)threadIdx.x * kScatterWpt;
+    if (q < W.q1) {  // q1 - q0 is a multiple of 64: all kScatterWpt starts are inside
+      RollingWindows rw;
+      rw.init(W, G.k, q);
+#pragma unroll
+      for (int j = 0; j < kScatterWpt; ++j) {
+        Window w;
+        if (rw.get(j, G.canonical, w)) {
+          const u64 h = key_hash(w.lo, w.hi);
+          if (G.n_parts <= 1 || owner_of(h, G.n_parts) == G.part) {
+            ++acc_valid;
+            const unsigned slot = j * kScatterThreads + threadIdx.x;
+            const unsigned p = part_of(h, P);
+            pr[j] = (p << 13) | atomicAdd(&s_cnt[p], 1u);
+            s_keys[(size_t)slot * KW] = w.lo;
+            if (KW == 2) s_keys[(size_t)slot * KW + 1] = w.hi;
+            s_info[slot] = info_of(w);
+          }
+        }
+        if (j + 1 < kScatterWpt) rw.roll();
       }
     }
     __syncthreads();
     // 2a: exclusive scan of the counts (each thread a contiguous chunk of partitions)
-    const unsigned per = (P + kPartThreads - 1) / kPartThreads;
+    const unsigned per = (P + kScatterThreads - 1) / kScatterThreads;
     const unsigned p0 = threadIdx.x * per, p1 = min(P, p0 + per);
     unsigned local = 0;
     for (unsigned p = p0; p < p1; ++p) local += s_cnt[p];
@@ -115,12 +208,12 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const __grid
     __syncthreads();
     if (threadIdx.x == 0) {
       unsigned run = 0;
-      for (int x = 0; x < kPartThreads / 32; ++x) {
+      for (int x = 0; x < kWarps; ++x) {
         const unsigned v = s_wsum[x];
         s_wsum[x] = run;
         run += v;
       }
-      s_wsum[8] = run;  // records in this tile
+      s_wsum[kWarps] = run;  // records in this tile
     }
     __syncthreads();
     unsigned run = s_wsum[warp] + incl - local;
@@ -146,12 +239,12 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const __grid
     for (int j = 0; j < kScatterWpt; ++j) {
       if (pr[j] == 0xFFFFFFFFu) continue;
       const unsigned p = pr[j] >> 13, r = pr[j] & 8191u;
-      s_order[s_off[p] + r] = (j * kPartThreads + threadIdx.x) | (p << 16);
+      s_order[s_off[p] + r] = (j * kScatterThreads + threadIdx.x) | (p << 16);
     }
     for (unsigned p = threadIdx.x; p < P; p += blockDim.x) s_cnt[p] = 0;  // for the next tile
     __syncthreads();
     // 3b: write out in sorted order (coalesced runs per bucket)
-    const unsigned total = s_wsum[8];
+    const unsigned total = s_wsum[kWarps];
     for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
       const unsigned e = s_order[i];
       const unsigned slot = e & 0xFFFFu, p = e >> 16;
@@ -177,7 +270,10 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const __grid
     }
     __syncthreads();  // staged records and per-partition runs are reused by the next tile
   }
-  if (lane == 0 && acc_valid) atomicAdd(&G.status->valid_windows, acc_valid);
+  // valid windows: reduce inside the warp first
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc_valid += __shfl_down_sync(0xffffffffu, acc_valid, o);
+  if (lane == 0 && acc_valid) atomicAdd(&G.status->valid_windows, (u64)acc_valid);
 }
 
 // ------------------------------------------------------------------ record pass
@@ -429,10 +525,10 @@ cudaError_t launch_part_scatter(const PartGeom& g, const PartWindows& w, const P
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const u64 tiles = (w.q1 - w.q0 + kScatterTile - 1) / kScatterTile;
-  u64 grid = grid_for(fn, kPartThreads, smem, num_sms);
+  u64 grid = grid_for(fn, kScatterThreads, smem, num_sms);
   if (grid > tiles) grid = tiles;
-  if (kw == 2) part_scatter_kernel<2><<<(unsigned)grid, kPartThreads, smem, stream>>>(g, w, r);
-  else part_scatter_kernel<1><<<(unsigned)grid, kPartThreads, smem, stream>>>(g, w, r);
+  if (kw == 2) part_scatter_kernel<2><<<(unsigned)grid, kScatterThreads, smem, stream>>>(g, w, r);
+  else part_scatter_kernel<1><<<(unsigned)grid, kScatterThreads, smem, stream>>>(g, w, r);
   return cudaGetLastError();
 }
 
