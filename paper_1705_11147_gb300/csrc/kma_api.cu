@@ -93,8 +93,13 @@ struct Derived {
   u64 staging;
   unsigned P;      // on-chip partitions (1: one table)
   u64 Wp, Sp;      // Bloom words / table slots per partition
+  u64 Wt;          // key filter words per partition (partitioned Bloom mode, else 0)
   u64 rec_bytes;   // bytes per record in partitioned mode
 };
+
+// Key filter of the partitioned recount: a second blocked Bloom filter that records the keys
+// inserted into the table, sized at this many bits per key the table is built for.
+constexpr double kKeyFilterBitsPerKey = 12.0;
 
 constexpr u64 kAutoPartitionAbove = 256ull << 20;  // filter + table bytes
 constexpr u64 kPartitionTarget = 48ull << 20;      // filter + table bytes per partition
@@ -159,6 +164,11 @@ int derive(const kma_params* p, Derived& d) {
     }
     d.plan.partitions = d.P;
     d.rec_bytes = (p->k > 32 ? 16 : 8) + 1;
+    if (P > 1 && p->use_bloom) {
+      const double lf = p->load_factor > 0 ? p->load_factor : 0.5;
+      const double keys = (double)d.plan.table_slots * lf;
+      d.Wt = std::max<u64>((u64)std::ceil(keys * kKeyFilterBitsPerKey / 64.0 / (double)P), 64);
+    }
   }
   // bit slices of the key hash address at most 2^32 Bloom words and 2^32 slots per partition
   if (d.plan.bloom_words >= (1ull << 32) || d.Sp >= (1ull << 32)) return KMA_EINVAL;
@@ -172,7 +182,7 @@ int derive(const kma_params* p, Derived& d) {
   d.plan.device_bytes = 2 * d.codes_words * 8 + 2 * d.bit_words * 8 + d.mark_words * 4 +
                         d.plan.bloom_words * 8 + d.plan.table_slots * sizeof(Slot) +
                         sizeof(DevStatus) + 2 * (2 * d.staging + (d.staging / 16 + 2) * 8);
-  if (d.P > 1) d.plan.device_bytes += (p->max_bases + p->max_bases / 16) * d.rec_bytes;
+  if (d.P > 1) d.plan.device_bytes += (p->max_bases + p->max_bases / 16) * d.rec_bytes + d.Wt * d.P * 8;
   return KMA_OK;
 }
 
@@ -222,6 +232,7 @@ struct kma_handle {
   u64* hq = nullptr;
   unsigned* marks = nullptr;
   u64* bloom = nullptr;
+  u64* keyfilter = nullptr;  // partitioned Bloom mode: keys inserted into the table
   Slot* table = nullptr;
   DevStatus* status = nullptr;
   DevStatus* host_status = nullptr;  // pinned
@@ -325,7 +336,7 @@ void free_records(kma_handle* h) {
 void free_all(kma_handle* h) {
   free_records(h);
   dfree(h, h->codes); dfree(h, h->rcodes); dfree(h, h->inv); dfree(h, h->hq); dfree(h, h->marks);
-  dfree(h, h->bloom); dfree(h, h->table); dfree(h, h->status);
+  dfree(h, h->bloom); dfree(h, h->keyfilter); dfree(h, h->table); dfree(h, h->status);
   for (int i = 0; i < 2; ++i) { dfree(h, h->stage_seq[i]); dfree(h, h->stage_qual[i]); dfree(h, h->stage_offs[i]); }
   dfree(h, h->out_keys); dfree(h, h->out_counts); dfree(h, h->out_ext); dfree(h, h->out_codes);
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -348,6 +359,7 @@ int clear_state(kma_handle* h) {
   free_records(h);
   KMA_CUDA(cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->stream));
   if (h->bloom) KMA_CUDA(cudaMemsetAsync(h->bloom, 0, h->d.plan.bloom_words * 8, h->stream));
+  if (h->keyfilter) KMA_CUDA(cudaMemsetAsync(h->keyfilter, 0, h->d.Wt * h->d.P * 8, h->stream));
   int rc = timed_launch(h, KMA_KERNEL_INIT, h->stream, h->d.plan.table_slots > 0,
                         [&] { return launch_table_init(h->table, h->d.plan.table_slots, h->stream); });
   if (rc) return rc;
@@ -433,6 +445,8 @@ PartGeom part_geom(kma_handle* h) {
   PartGeom g;
   std::memset(&g, 0, sizeof(g));
   g.bloom = h->bloom;
+  g.keyfilter = h->keyfilter;
+  g.Wk = h->d.Wt;
   g.table = h->table;
   g.status = h->status;
   g.Wp = h->d.Wp;
@@ -591,7 +605,7 @@ int kmer_analysis_create(const kma_params* params, void* cuda_stream, kma_handle
   if ((rc = dalloc(h, &h->codes, d.codes_words)) || (rc = dalloc(h, &h->rcodes, d.codes_words)) ||
       (rc = dalloc(h, &h->inv, d.bit_words)) ||
       (rc = dalloc(h, &h->hq, d.bit_words)) || (rc = dalloc(h, &h->marks, d.mark_words)) ||
-      (rc = dalloc(h, &h->bloom, d.plan.bloom_words)) ||
+      (rc = dalloc(h, &h->bloom, d.plan.bloom_words)) || (rc = dalloc(h, &h->keyfilter, d.Wt * d.P)) ||
       (rc = dalloc(h, &h->table, d.plan.table_slots)) || (rc = dalloc(h, &h->status, 1))) {
     free_all(h);
     delete h;
@@ -716,6 +730,9 @@ static int enqueue_recount(kma_handle* const* hs, uint32_t n) {
     kma_handle* h = hs[i];
     if (!h->p.use_bloom || h->d.P <= 1) continue;
     const PartGeom g = part_geom(h);
+    rc = timed_launch(h0, KMA_KERNEL_RECOUNT, h0->stream, g.Wk > 0,
+                      [&] { return launch_keyfilter_build(g, h0->stream, h0->num_sms); });
+    if (rc) return rc;
     for (auto& rb : h->rec_batches) {
       PartRecords r;
       r.keys = rb.keys; r.info = rb.info; r.cap = rb.cap; r.ocap = rb.ocap; r.fill = rb.fill;

@@ -56,6 +56,19 @@ __device__ __forceinline__ u64 bloom_mask(u64 h, unsigned nbits) {
   return m;
 }
 
+// Key filter (partitioned recount): one 64-bit word per key, chosen by the low half of
+// h * phi (the table slot uses its high half), bits from the top of (h ^ h >> 32) * c' with a
+// multiplier of its own.
+__device__ __forceinline__ u64 keyfilter_index(u64 h, u64 words) {
+  return __umulhi((unsigned)scramble(h), (unsigned)words);
+}
+__device__ __forceinline__ u64 keyfilter_mask(u64 h, unsigned nbits) {
+  const u64 g = (h ^ (h >> 32)) * 0x94d049bb133111ebull;
+  u64 m = 0;
+  for (unsigned i = 0; i < nbits; ++i) m |= 1ull << ((g >> (58 - 6 * i)) & 63);
+  return m;
+}
+
 // L2 cache policy for data read or written once (record streams): evict first, so the
 // partition's Bloom sub-filter and sub-table stay resident.
 __device__ __forceinline__ u64 policy_evict_first() {

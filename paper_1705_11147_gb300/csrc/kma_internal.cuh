@@ -158,8 +158,10 @@ struct PartGeom {
   unsigned long long* bloom;
   Slot* table;
   DevStatus* status;
+  unsigned long long* keyfilter;  // Bloom mode: blocked Bloom filter of the keys in the table
   unsigned long long Wp;        // Bloom words per partition
   unsigned long long Sp;        // table slots per partition
+  unsigned long long Wk;        // key-filter words per partition (0: no key filter)
   unsigned int P;
   unsigned int bloom_h;
   unsigned int k;
@@ -199,6 +201,8 @@ cudaError_t launch_part_scatter(const PartGeom& g, const PartWindows& w, const P
                                 cudaStream_t stream, int num_sms);
 cudaError_t launch_part_pass(const PartGeom& g, const PartRecords& r, unsigned mode,
                              cudaStream_t stream, int num_sms);
+// Key filter of the recount: set by every key in the table (after the Bloom pass).
+cudaError_t launch_keyfilter_build(const PartGeom& g, cudaStream_t stream, int num_sms);
 
 struct LaunchShape {
   int block_threads;

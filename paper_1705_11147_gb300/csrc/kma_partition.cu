@@ -344,7 +344,7 @@ __device__ __forceinline__ void rec_issue(WarpStage<KW, RPT>& S, const PartRecor
 __device__ __forceinline__ u64 shfl0(u64 v) { return __shfl_sync(0xffffffffu, v, 0); }
 
 template <int KW, int RPT, unsigned MODE>
-__global__ void __launch_bounds__(kPartThreads) part_pass_kernel(const __grid_constant__ PartGeom G,
+__global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount ? 6 : 4) : 2) part_pass_kernel(const __grid_constant__ PartGeom G,
                                                                  const __grid_constant__ PartRecords R) {
   constexpr int kTile = WarpStage<KW, RPT>::kTile;
   constexpr int kWarps = kPartThreads / 32;
@@ -459,6 +459,16 @@ __global__ void __launch_bounds__(kPartThreads) part_pass_kernel(const __grid_co
         act[j] = act[j] && !first;
       }
     }
+    // recount: most first sightings are of k-mers seen once, which never reached the table;
+    // the key filter (every inserted key sets its bits) rules them out without a probe
+    if (MODE == kModeRecount && G.Wk) {
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) {
+        if (!act[j]) continue;
+        const u64 m = keyfilter_mask(h[j], G.bloom_h);
+        act[j] = (__ldcg(G.keyfilter + (u64)p[j] * G.Wk + keyfilter_index(h[j], G.Wk)) & m) == m;
+      }
+    }
     // stage 3: first probe in the partition's sub-table
     ulonglong2 kv[RPT];
     u64 idx[RPT];
@@ -502,6 +512,34 @@ __global__ void __launch_bounds__(kPartThreads) part_pass_kernel(const __grid_co
   if (lane == 0) {
     if (acc_ins) atomicAdd(&G.status->table_keys, acc_ins);
     if (acc_first) atomicAdd(&G.status->first_sightings, acc_first);
+  }
+}
+
+// ------------------------------------------------------------------ key filter
+//
+// After the Bloom pass: every key in the table sets its bits in its partition's key filter.
+// One CTA chunk = kKeyChunk consecutive slots of one partition (slot keys read once, in order).
+
+constexpr int kKeyThreads = 256;
+constexpr int kKeyChunk = kKeyThreads * 8;
+
+__global__ void __launch_bounds__(kKeyThreads) keyfilter_build_kernel(const __grid_constant__ PartGeom G) {
+  const u64 chunks_per_part = (G.Sp + kKeyChunk - 1) / kKeyChunk;
+  const u64 n_chunks = chunks_per_part * G.P;
+  for (u64 c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    const u64 p = c / chunks_per_part;
+    const u64 s0 = (c - p * chunks_per_part) * kKeyChunk;
+    const Slot* sub = G.table + p * G.Sp;
+    u64* kf = G.keyfilter + p * G.Wk;
+#pragma unroll
+    for (int j = 0; j < kKeyChunk / kKeyThreads; ++j) {
+      const u64 i = s0 + (u64)j * kKeyThreads + threadIdx.x;
+      if (i >= G.Sp) break;
+      const ulonglong2 kv = __ldcs(reinterpret_cast<const ulonglong2*>(sub + i));
+      if (kv.x == kEmpty && kv.y == kEmpty) continue;
+      const u64 h = key_hash(kv.x, kv.y);
+      atomicOr(kf + keyfilter_index(h, G.Wk), keyfilter_mask(h, G.bloom_h));
+    }
   }
 }
 
@@ -552,6 +590,15 @@ static cudaError_t launch_pass_mode(const PartGeom& g, const PartRecords& r, uns
   if (mode == kModeBloom) return launch_pass_rt<KW, RPT, kModeBloom>(g, r, stream, num_sms);
   if (mode == kModeCount) return launch_pass_rt<KW, RPT, kModeCount>(g, r, stream, num_sms);
   return launch_pass_rt<KW, RPT, kModeRecount>(g, r, stream, num_sms);
+}
+
+cudaError_t launch_keyfilter_build(const PartGeom& g, cudaStream_t stream, int num_sms) {
+  if (!g.Wk || !g.keyfilter) return cudaSuccess;
+  const u64 chunks = g.P * ((g.Sp + kKeyChunk - 1) / kKeyChunk);
+  u64 grid = grid_for((const void*)keyfilter_build_kernel, kKeyThreads, 0, num_sms);
+  if (grid > chunks) grid = chunks;
+  keyfilter_build_kernel<<<(unsigned)grid, kKeyThreads, 0, stream>>>(g);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_part_pass(const PartGeom& g, const PartRecords& r, unsigned mode, cudaStream_t stream,
