@@ -519,16 +519,15 @@ __global__ void __launch_bounds__(256) query_kernel(const Slot* table, u64 slots
 
 // ------------------------------------------------------------------ table init
 
+// Consecutive threads write consecutive 16-byte pieces of the table (every warp store covers
+// 512 contiguous bytes): the key piece of a slot gets the empty pattern, the rest zero.
 __global__ void __launch_bounds__(256) table_init_kernel(Slot* table, u64 slots) {
   const u64 stride = (u64)gridDim.x * blockDim.x;
-  const ulonglong2 empty = make_ulonglong2(kEmpty, kEmpty);
-  const ulonglong2 zero = make_ulonglong2(0, 0);
-  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
-    ulonglong2* s = reinterpret_cast<ulonglong2*>(table + i);
-    __stcg(s + 0, empty);
-    __stcg(s + 1, zero);
-    __stcg(s + 2, zero);
-    __stcg(s + 3, zero);
+  const u64 pieces = slots * (sizeof(Slot) / 16);
+  ulonglong2* t = reinterpret_cast<ulonglong2*>(table);
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < pieces; i += stride) {
+    const u64 v = (i & 3) == 0 ? kEmpty : 0ull;
+    __stcs(t + i, make_ulonglong2(v, v));
   }
 }
 
