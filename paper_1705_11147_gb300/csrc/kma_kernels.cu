@@ -43,7 +43,7 @@ __device__ __forceinline__ int find_pass_sample(const PassBatch& B, u64 t) {
 // together: all Bloom atomics (with an L2 prefetch of each window's first table slot) are in
 // flight at once, then all first probes, then the updates.
 template <int WPT, bool AGG>
-__global__ void __launch_bounds__(256) pass_kernel(const __grid_constant__ PassBatch B) {
+__global__ void __launch_bounds__(256, WPT <= 2 ? 4 : 1) pass_kernel(const __grid_constant__ PassBatch B) {
   const unsigned lane = threadIdx.x & 31;
   const u64 tile = (u64)blockDim.x * WPT;
   // Per-warp running totals, flushed when the warp moves to another sample.
