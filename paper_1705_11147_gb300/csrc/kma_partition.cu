@@ -40,16 +40,16 @@ constexpr int kPartThreads = 256;
 //  3. permute the staged records into partition order and write them out: consecutive
 //     threads write consecutive records of the same bucket, so the stores coalesce.
 
-constexpr int kScatterThreads = 512;
+constexpr int kScatterThreads = 1024;
 constexpr int kScatterWpt = 8;
-constexpr int kScatterTile = kScatterThreads * kScatterWpt;  // 4096 (< 2^13: ranks and slots fit)
+constexpr int kScatterTile = kScatterThreads * kScatterWpt;  // 8192 (ranks < 2^13, slots < 2^16)
 
 __host__ __device__ constexpr size_t scatter_smem(unsigned P, int kw) {
   return (size_t)kScatterTile * (kw * 8) +   // staged keys
          (size_t)kScatterTile +              // staged info
          (size_t)kScatterTile * 4 +          // sorted order: slot | partition << 16
          (size_t)P * (4 + 4 + 4 + 8 + 8) +   // cnt, off, n1, gbase, obase
-         256;                                // warp sums, tile total, alignment
+         512;                                // warp sums, tile total, alignment
 }
 
 // kScatterWpt consecutive windows starting at q (a multiple of 8), one at a time: the state
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kScatterThreads) part_scatter_kernel(const __g
   unsigned* s_off = s_cnt + P;                                                   // [P]
   unsigned* s_n1 = s_off + P;                                                    // [P]
   unsigned* s_wsum = s_n1 + P;                                                   // [kWarps + 1]
-  unsigned char* s_info = reinterpret_cast<unsigned char*>(s_wsum + 32);         // [tile]
+  unsigned char* s_info = reinterpret_cast<unsigned char*>(s_wsum + 64);         // [tile]
   const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u64 n_tiles = (W.q1 - W.q0 + kScatterTile - 1) / kScatterTile;
   const u64 pol = policy_evict_first();
