@@ -80,7 +80,8 @@ def expand(candidate: dict, base: dict) -> dict:
     if p < 0:
         auto = plan(make_params(**{**base, **{kk: v for kk, v in c.items() if kk != "partitions"},
                                    "partitions": 0})).partitions
-        c["partitions"] = max(1, min(4096, auto * (-p)))
+        k = c.get("k", base.get("k", 31))
+        c["partitions"] = max(1, min(2048 if k > 32 else 4096, auto * (-p)))
     return c
 
 

@@ -120,7 +120,7 @@ int check_params(const kma_params* p) {
     return KMA_EINVAL;
   if (p->slot_prefetch > 2) return KMA_EINVAL;
   if (p->fault_inject > 1) return KMA_EINVAL;
-  if (p->partitions > kMaxPartitions) return KMA_EINVAL;
+  if (p->partitions > (p->k > 32 ? kMaxPartitionsWide : kMaxPartitions)) return KMA_EINVAL;
   if (p->n_parts > 1 && p->part >= p->n_parts) return KMA_EINVAL;
   return KMA_OK;
 }
@@ -149,7 +149,8 @@ int derive(const kma_params* p, Derived& d) {
     const u64 bytes = W * 8 + S * sizeof(Slot);
     u64 P = p->partitions;
     if (P == 0) P = bytes > kAutoPartitionAbove ? (bytes + kPartitionTarget - 1) / kPartitionTarget : 1;
-    if (P > kMaxPartitions) P = kMaxPartitions;
+    const u64 max_parts = p->k > 32 ? kMaxPartitionsWide : kMaxPartitions;
+    if (P > max_parts) P = max_parts;
     if (P < 1) P = 1;
     d.P = (unsigned)P;
     d.Wp = (W + P - 1) / P;

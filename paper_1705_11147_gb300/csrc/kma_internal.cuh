@@ -148,7 +148,8 @@ struct ClassBatch {
 // [p*Wp, (p+1)*Wp) and table slots [p*Sp, (p+1)*Sp). Windows are first scattered into
 // per-partition record buckets (streaming writes), then the buckets are processed in order,
 // so the random Bloom/table traffic of one partition stays in L2.
-constexpr unsigned kMaxPartitions = 4096;
+constexpr unsigned kMaxPartitions = 4096;      // k <= 32 (one-word keys)
+constexpr unsigned kMaxPartitionsWide = 2048;  // k > 32: the scatter's staged tile is larger
 
 // Record info byte: bits 0-1 left base, bit 2 left usable, bits 3-4 right base,
 // bit 5 right usable, bit 7 first sighting (set by the Bloom pass).

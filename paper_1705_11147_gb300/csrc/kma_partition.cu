@@ -52,6 +52,9 @@ __host__ __device__ constexpr size_t scatter_smem(unsigned P, int kw) {
          512;                                // warp sums, tile total, alignment
 }
 
+static_assert(scatter_smem(kMaxPartitions, 1) <= 227 * 1024 && scatter_smem(kMaxPartitionsWide, 2) <= 227 * 1024,
+              "the scatter's shared memory must fit one CTA for every allowed partition count");
+
 // kScatterWpt consecutive windows starting at q (a multiple of 8), one at a time: the state
 // holds the forward k-mer F and its reverse complement R of the current window, the next
 // bases to enter (MSB first), and the invalid / high-quality bits around the windows.

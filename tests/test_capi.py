@@ -154,6 +154,10 @@ def test_partition_sizing(lib):
     one = _plan(k=31, max_bases=6_000_000_000, expected_distinct=2_100_000_000, partitions=1)
     assert one.partitions == 1
     assert _plan_rc(k=31, max_bases=1000, partitions=5000) == capi.KMA_EINVAL
+    # two-word keys stage larger scatter tiles: at most 2048 partitions
+    assert _plan(k=31, max_bases=1_000_000, partitions=3000).partitions == 3000
+    assert _plan_rc(k=51, max_bases=1_000_000, partitions=3000) == capi.KMA_EINVAL
+    assert _plan(k=51, max_bases=1_000_000, partitions=2048).partitions == 2048
 
 
 def test_missing_library_fails_loudly(tmp_path):
