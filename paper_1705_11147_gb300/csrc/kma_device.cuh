@@ -20,8 +20,10 @@ __device__ __forceinline__ u64 fmix64(u64 x) {
   return x;
 }
 
+// 64-bit hash of a 128-bit key: the high word is spread by an odd multiplier (plus a
+// constant), folded into the low word, and the result mixed by one finaliser.
 __device__ __forceinline__ u64 key_hash(u64 lo, u64 hi) {
-  return fmix64(lo ^ fmix64(hi + 0x9e3779b97f4a7c15ull));
+  return fmix64(lo ^ (hi * 0x9e3779b97f4a7c15ull + 0x632be59bd9b4e019ull));
 }
 
 // Everything derived from the 64-bit key hash h uses cheap 32-bit slices of h and of two
@@ -49,11 +51,19 @@ __device__ __forceinline__ unsigned part_of(u64 h, unsigned P) {
   return __umulhi((unsigned)(h >> 32), P);
 }
 
+// Mask with bit x set for each 6-bit field x taken from the top of g (built in 32-bit halves).
+__device__ __forceinline__ u64 mask_from_fields(u64 g, unsigned nbits) {
+  unsigned lo = 0, hi = 0;
+  for (unsigned i = 0; i < nbits; ++i) {
+    const unsigned x = (unsigned)(g >> (58 - 6 * i)) & 63u;
+    const unsigned bit = 1u << (x & 31u);
+    if (x & 32u) hi |= bit; else lo |= bit;
+  }
+  return ((u64)hi << 32) | lo;
+}
+
 __device__ __forceinline__ u64 bloom_mask(u64 h, unsigned nbits) {
-  const u64 g = (h ^ (h >> 32)) * 0xd6e8feb86659fd93ull;
-  u64 m = 0;
-  for (unsigned i = 0; i < nbits; ++i) m |= 1ull << ((g >> (58 - 6 * i)) & 63);
-  return m;
+  return mask_from_fields((h ^ (h >> 32)) * 0xd6e8feb86659fd93ull, nbits);
 }
 
 // Key filter (partitioned recount): one 64-bit word per key, chosen by the low half of
@@ -63,10 +73,7 @@ __device__ __forceinline__ u64 keyfilter_index(u64 h, u64 words) {
   return __umulhi((unsigned)scramble(h), (unsigned)words);
 }
 __device__ __forceinline__ u64 keyfilter_mask(u64 h, unsigned nbits) {
-  const u64 g = (h ^ (h >> 32)) * 0x94d049bb133111ebull;
-  u64 m = 0;
-  for (unsigned i = 0; i < nbits; ++i) m |= 1ull << ((g >> (58 - 6 * i)) & 63);
-  return m;
+  return mask_from_fields((h ^ (h >> 32)) * 0x94d049bb133111ebull, nbits);
 }
 
 // L2 cache policy for data read or written once (record streams): evict first, so the

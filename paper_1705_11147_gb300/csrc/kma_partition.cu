@@ -306,7 +306,7 @@ __device__ __forceinline__ bool rec_tile(const PartGeom& G, const PartRecords& R
                                          u64& end) {
   u64 f, lo, b0;
   if (t < (u64)G.P * tpb) {
-    const u64 b = t / tpb;
+    const u64 b = ((t | tpb) >> 32) ? t / tpb : (u64)((unsigned)t / (unsigned)tpb);
     f = R.fill[b] < R.cap ? R.fill[b] : R.cap;
     lo = (t - b * tpb) * TILE;
     b0 = b * R.cap;
