@@ -379,6 +379,19 @@ def run_ours(args, ws, rank, local):
     kernel_ms = {k2[3:]: round(v / args.steps, 3) for k2, v in timing.items() if k2.startswith("ms_")}
     launches = int(timing["launches"])
 
+    # Section 5.1's cardinality pass, timed once on the resident reads (not part of the step:
+    # the step is sized from the workload recipe, as a user who knows the genome would)
+    from paper_1705_11147_gb300 import estimate_distinct
+    estimate_distinct(seq, qual, offs, k=k, canonical=bool(prm.canonical), stream=stream)  # warm
+    torch.cuda.synchronize(dev)
+    t_est = time.perf_counter()
+    est = estimate_distinct(seq, qual, offs, k=k, canonical=bool(prm.canonical), stream=stream)
+    t_est = time.perf_counter() - t_est
+    sizing = {"ms": round(t_est * 1e3, 2), "distinct_estimate": round(est.distinct),
+              "rel_std_error": round(est.rel_std_error, 5), "precision": est.precision,
+              "recipe_expected_distinct": int(prm.expected_distinct),
+              "what": "HyperLogLog pass (pack + sketch, temporary arena), host wall time"}
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, ka, rs, dev, qkeys, ws)
@@ -401,7 +414,7 @@ def run_ours(args, ws, rank, local):
            "tuning": {k2: getattr(prm, k2) for k2 in ("block_threads", "windows_per_thread", "ctas_per_sm",
                                                       "warp_aggregate", "slot_prefetch", "partitions")}
                      | {"partitions_used": int(plan_used.partitions)},
-           "clocks": clk, "generation_s": round(t_gen, 1)}
+           "clocks": clk, "generation_s": round(t_gen, 1), "sizing_pass": sizing}
     if e2e:
         out["e2e"] = e2e
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -543,7 +556,7 @@ def run_batched(args, ws, rank, local):
             "plain": {"value": round(plain_value, 3), "unit": UNIT, "ms_per_step": round(ms_plain, 2),
                       "path": "create -> count -> finalize -> destroy per sample"},
             "batched_vs_plain": round(value / plain_value, 3), "gpu_launches": int(launches),
-            "clocks": clk, "generation_s": round(t_gen, 1)}
+            "clocks": clk, "generation_s": round(t_gen, 1), "sizing_pass": sizing}
 
 
 # ------------------------------------------------------------------ served (job stream)

@@ -284,6 +284,42 @@ int kmer_analysis_count_small_noalloc(const kma_params* params, const char* seq,
                                       uint8_t* codes, uint64_t capacity, uint64_t* n_out,
                                       void* cuda_stream);
 
+/* ---- Cardinality estimate (Section 5.1: a HyperLogLog pass sizes the Bloom filter) --------
+ * Estimates the number of distinct canonical k-mers of a read set with a HyperLogLog sketch
+ * of m = 2^precision registers (64-bit hashes, as in Section 5.1): every valid window's key
+ * (with n_parts > 1: every key owned by `part`) is hashed; the top `precision` bits of the
+ * hash pick a register, which keeps the largest rank seen, rank = 1 + leading zeros of the
+ * remaining bits. Relative standard error 1.04 / sqrt(m) (0.8 % at the default m = 2^14).
+ * The sketch depends only on the set of distinct keys; sketches merge by elementwise
+ * maximum (several batches of reads, or the owner partitions of several GPUs). */
+#define KMA_HLL_MIN_PRECISION 4
+#define KMA_HLL_MAX_PRECISION 14
+
+typedef struct {
+  uint32_t precision;       /* in: p (KMA_HLL_MIN_PRECISION .. KMA_HLL_MAX_PRECISION; 0 = 14) */
+  uint32_t pad;
+  double distinct;          /* out: estimated distinct canonical k-mers (of the merged sketch) */
+  double rel_std_error;     /* out: 1.04 / sqrt(2^p) */
+  uint64_t valid_windows;   /* out: valid windows this call saw (exact; owned keys only) */
+} kma_estimate;
+
+/* One estimation pass over reads given like kmer_analysis_count's (host pointers, or device
+ * pointers with on_device = 1). params->k, canonical, n_parts and part are used, plus
+ * max_bases / max_reads as lower bounds of the temporary read arena (the call allocates what
+ * the reads need, packs them with the counting path's kernel, runs the sketch kernel and
+ * frees everything before it returns; it synchronises `cuda_stream`). `registers`, if not
+ * NULL, is a host array of 2^p bytes: on entry a sketch to merge with (all zero = empty), on
+ * return the merged sketch; the estimate is that of the merged sketch.
+ * Errors: KMA_EINVAL (params, precision, offsets), KMA_ENOMEM, KMA_ECUDA. */
+int kmer_analysis_estimate(const kma_params* params, const char* seq, const char* qual,
+                           const uint64_t* offsets, uint64_t n_reads, int on_device,
+                           void* cuda_stream, kma_estimate* est, uint8_t* registers);
+
+/* The estimate of a sketch (host only, no GPU): E = alpha_m m^2 / sum_j 2^-M[j], replaced by
+ * linear counting m ln(m / V) when E <= 5m/2 and V registers are zero (Flajolet et al. 2007;
+ * with 64-bit hashes no large-range correction). KMA_EINVAL on a bad precision. */
+int kmer_analysis_hll_estimate(const uint8_t* registers, uint32_t precision, double* distinct);
+
 #ifdef __cplusplus
 }
 #endif

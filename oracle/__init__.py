@@ -50,6 +50,9 @@ def _lib():
         lib.oracle_partition_of.argtypes = [p, u64, u32, u32, p]
         lib.oracle_pack_strings.argtypes = [ctypes.c_char_p, u64, u32, p]
         lib.oracle_unpack_keys.argtypes = [p, u64, u32, p]
+        lib.oracle_hll_registers.argtypes = [p, u64, u32, p]
+        lib.oracle_hll_estimate.argtypes = [p, u32]
+        lib.oracle_hll_estimate.restype = ctypes.c_double
         _LIB = lib
     return _LIB
 
@@ -162,3 +165,19 @@ def reads_from_strings(reads: list[str], quals: list[str] | None = None, default
     offs = np.zeros(len(reads) + 1, np.uint64)
     offs[1:] = np.cumsum([len(r) for r in reads])
     return seq, qual, offs
+
+
+def hll_registers(keys: np.ndarray, precision: int) -> np.ndarray:
+    """HyperLogLog sketch (2^precision uint8 registers) of a set of distinct keys
+    (Section 5.1's cardinality pass, written from its definition in kmer_oracle.cpp)."""
+    q = np.ascontiguousarray(keys, dtype=np.uint64).reshape(-1, 2)
+    out = np.zeros(1 << precision, np.uint8)
+    _lib().oracle_hll_registers(q.ctypes.data, q.shape[0], precision, out.ctypes.data)
+    return out
+
+
+def hll_estimate(registers: np.ndarray, precision: int) -> float:
+    """Flajolet et al.'s estimate (with linear counting in the small range) of a sketch."""
+    r = np.ascontiguousarray(registers, dtype=np.uint8)
+    assert r.shape == (1 << precision,)
+    return float(_lib().oracle_hll_estimate(r.ctypes.data, precision))

@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <array>
 #include <cstdint>
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <memory_resource>
@@ -375,6 +376,62 @@ void oracle_unpack_keys(const uint64_t* keys, uint64_t n, uint32_t k, char* out)
     std::string s = unpack(Key{keys[2 * i], keys[2 * i + 1]}, k);
     std::memcpy(out + i * k, s.data(), k);
   }
+}
+
+// ---- HyperLogLog sketch (Section 5.1's cardinality pass), from its definition ----------
+// The sketch of a set of distinct keys with m = 2^p registers: each key (lo, hi) is hashed to
+// 64 bits by the sketch's hash h = fmix64(lo XOR (hi * 0x9e3779b97f4a7c15 + 0x632be59bd9b4e019)),
+// fmix64 being the MurmurHash3 64-bit finaliser (Appleby); register j = the top p bits of h;
+// the register holds the largest rank over its keys, rank = 1 + number of leading zeros of
+// the other 64 - p bits (64 - p + 1 if they are all zero). Written here on its own; the hash
+// is part of the sketch's definition, so both sides must agree on it bit for bit.
+
+uint64_t sketch_fmix64(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+void oracle_hll_registers(const uint64_t* keys, uint64_t n, uint32_t p, uint8_t* regs) {
+  const uint64_t m = 1ull << p;
+  for (uint64_t j = 0; j < m; ++j) regs[j] = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint64_t lo = keys[2 * i], hi = keys[2 * i + 1];
+    const uint64_t h = sketch_fmix64(lo ^ (hi * 0x9e3779b97f4a7c15ull + 0x632be59bd9b4e019ull));
+    const uint64_t j = h >> (64 - p);
+    // leading zeros of the remaining 64 - p bits, counted one bit at a time
+    uint32_t rank = 1;
+    for (uint32_t b = 0; b < 64 - p; ++b) {
+      if ((h >> (63 - p - b)) & 1) break;
+      ++rank;
+    }
+    if (rank > regs[j]) regs[j] = (uint8_t)rank;
+  }
+}
+
+// Flajolet, Fusy, Gandouet, Meunier (2007): E = alpha_m m^2 / sum_j 2^(-M[j]); if E <= 5m/2
+// and V > 0 registers are zero, E = m ln(m / V) (linear counting). With 64-bit hashes the
+// large-range correction of the 32-bit original is not needed.
+double oracle_hll_estimate(const uint8_t* regs, uint32_t p) {
+  const uint64_t m = 1ull << p;
+  const double md = (double)m;
+  double alpha;
+  if (m == 16) alpha = 0.673;
+  else if (m == 32) alpha = 0.697;
+  else if (m == 64) alpha = 0.709;
+  else alpha = 0.7213 / (1.0 + 1.079 / md);
+  double sum = 0.0;
+  uint64_t zeros = 0;
+  for (uint64_t j = 0; j < m; ++j) {
+    sum += std::pow(2.0, -(double)regs[j]);
+    if (regs[j] == 0) ++zeros;
+  }
+  const double e = alpha * md * md / sum;
+  if (e <= 2.5 * md && zeros > 0) return md * std::log(md / (double)zeros);
+  return e;
 }
 
 }  // extern "C"

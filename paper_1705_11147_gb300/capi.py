@@ -59,6 +59,14 @@ class kma_timings(ctypes.Structure):
 KERNEL_KINDS = ("pack", "pass", "recount", "classify", "query", "init", "unused", "scatter")
 
 
+class kma_estimate(ctypes.Structure):
+    _fields_ = [("precision", u32), ("pad", u32), ("distinct", dbl), ("rel_std_error", dbl),
+                ("valid_windows", u64)]
+
+
+HLL_MIN_PRECISION, HLL_MAX_PRECISION = 4, 14
+
+
 class kma_reads(ctypes.Structure):
     _fields_ = [("seq", vp), ("qual", vp), ("offsets", vp), ("n_reads", u64), ("n_bases", u64)]
 
@@ -85,6 +93,9 @@ _SIGS = {
     "kmer_analysis_fetch_result": ([vp, ctypes.POINTER(kma_result)], ctypes.c_int),
     "kmer_analysis_count_small_noalloc": ([ctypes.POINTER(kma_params), vp, vp, vp, u64, u64, vp, vp,
                                            vp, vp, u64, ctypes.POINTER(u64), vp], ctypes.c_int),
+    "kmer_analysis_estimate": ([ctypes.POINTER(kma_params), vp, vp, vp, u64, ctypes.c_int, vp,
+                                ctypes.POINTER(kma_estimate), vp], ctypes.c_int),
+    "kmer_analysis_hll_estimate": ([vp, u32, ctypes.POINTER(dbl)], ctypes.c_int),
 }
 
 _LIB = None

@@ -250,6 +250,7 @@ struct kma_handle {
   u64 count_bound = 0;
   bool finalized = false;
   bool failed = false;
+  bool pack_only = false;  // estimation handles: count() packs the reads, no counting pass
 
   // partitioned mode: per-partition histogram / cursors and the record buckets of each
   // count() batch (kept until finalize has recounted them)
@@ -532,6 +533,7 @@ int run_pack_and_pass(kma_handle* h, const PackDesc& pd) {
   int rc = timed_launch(h, KMA_KERNEL_PACK, h->stream, pb.total_chunks > 0,
                         [&] { return launch_pack(pb, h->stream, h->num_sms); });
   if (rc) return rc;
+  if (h->pack_only) return KMA_OK;
   return first_pass(h, pd.q0, pd.n_pos, pd.n_reads, pd.n_bases, h->stream);
 }
 
@@ -572,6 +574,24 @@ void fill_result(kma_handle* h) {
   r.counts = h->out_counts;
   r.ext = h->out_ext;
   r.codes = h->out_codes;
+}
+
+// HyperLogLog estimate of 2^p registers (Flajolet, Fusy, Gandouet, Meunier 2007): the raw
+// estimate alpha_m m^2 / sum 2^-M[j], replaced by linear counting m ln(m / V) in the small
+// range (raw <= 5m/2 with V > 0 empty registers). 64-bit hashes need no large-range
+// correction.
+double hll_estimate(const uint8_t* regs, unsigned p) {
+  const double m = (double)(1u << p);
+  double sum = 0.0;
+  u64 zeros = 0;
+  for (u64 j = 0; j < (1ull << p); ++j) {
+    sum += std::ldexp(1.0, -(int)regs[j]);
+    zeros += regs[j] == 0;
+  }
+  const double alpha = p == 4 ? 0.673 : p == 5 ? 0.697 : p == 6 ? 0.709 : 0.7213 / (1.0 + 1.079 / m);
+  const double raw = alpha * m * m / sum;
+  if (raw <= 2.5 * m && zeros > 0) return m * std::log(m / (double)zeros);
+  return raw;
 }
 
 }  // namespace
@@ -698,7 +718,7 @@ int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual, const 
                            [&] { return launch_pack(pb, h->stream, h->num_sms); })))
       return rc;
     KMA_CUDA(cudaEventRecord(h->consumed[b], h->stream));
-    if ((rc = first_pass(h, q0, n_pos, r1 - r0, nb, h->stream))) return rc;
+    if (!h->pack_only && (rc = first_pass(h, q0, n_pos, r1 - r0, nb, h->stream))) return rc;
     r0 = r1;
   }
   // Host buffers may be reused once the call returns: wait for the copies.
@@ -1041,6 +1061,90 @@ int kmer_analysis_timings(kma_handle* h, kma_timings* out, int reset) {
     for (int i = 0; i < 8; ++i) { h->ms[i] = 0; h->launches[i] = 0; }
   }
   return KMA_OK;
+}
+
+int kmer_analysis_hll_estimate(const uint8_t* registers, uint32_t precision, double* distinct) {
+  if (!registers || !distinct || precision < KMA_HLL_MIN_PRECISION || precision > KMA_HLL_MAX_PRECISION)
+    return KMA_EINVAL;
+  *distinct = hll_estimate(registers, precision);
+  return KMA_OK;
+}
+
+int kmer_analysis_estimate(const kma_params* params, const char* seq, const char* qual,
+                           const uint64_t* offsets, uint64_t n_reads, int on_device, void* cuda_stream,
+                           kma_estimate* est, uint8_t* registers) {
+  if (!params || !est || !offsets) return KMA_EINVAL;
+  const unsigned p = est->precision ? est->precision : 14;
+  if (p < KMA_HLL_MIN_PRECISION || p > KMA_HLL_MAX_PRECISION) return KMA_EINVAL;
+  if (n_reads && (!seq || !qual)) return KMA_EINVAL;
+  int rc = check_params(params);
+  if (rc) return rc;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  // bases of the read set (device offsets: read back the two ends)
+  u64 ends[2] = {0, 0};
+  if (n_reads) {
+    if (on_device) {
+      KMA_CUDA(cudaMemcpyAsync(&ends[0], offsets, 8, cudaMemcpyDeviceToHost, stream));
+      KMA_CUDA(cudaMemcpyAsync(&ends[1], offsets + n_reads, 8, cudaMemcpyDeviceToHost, stream));
+      KMA_CUDA(cudaStreamSynchronize(stream));
+    } else {
+      ends[0] = offsets[0];
+      ends[1] = offsets[n_reads];
+    }
+    if (ends[1] < ends[0]) return KMA_EINVAL;
+  }
+  // a handle that only packs: the read arena, no Bloom filter, a token table
+  kma_params q = *params;
+  q.use_bloom = 0;
+  q.table_capacity = 64;
+  q.expected_keys = 0;
+  q.expected_distinct = 0;
+  q.partitions = 1;
+  q.fault_inject = 0;
+  q.max_bases = std::max<u64>(q.max_bases, std::max<u64>(ends[1] - ends[0], 1));
+  q.max_reads = std::max<u64>(q.max_reads, std::max<u64>(n_reads, 1));
+  kma_handle* h = nullptr;
+  if ((rc = kmer_analysis_create(&q, cuda_stream, &h))) return rc;
+  h->pack_only = true;
+  const u64 m = 1ull << p;
+  std::vector<unsigned> regs32(m, 0);
+  if (registers)
+    for (u64 j = 0; j < m; ++j) regs32[j] = registers[j];
+  unsigned* d_regs = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync((void**)&d_regs, m * 4, h->pool, h->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    kmer_analysis_destroy(h);
+    return e == cudaErrorMemoryAllocation ? KMA_ENOMEM : cuda_fail(e, "sketch registers");
+  }
+  auto finish = [&](int code) {
+    cudaFreeAsync(d_regs, h->stream);
+    kmer_analysis_destroy(h);
+    return code;
+  };
+  if ((e = cudaMemcpyAsync(d_regs, regs32.data(), m * 4, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+    return finish(cuda_fail(e, "sketch registers in"));
+  if (n_reads && (rc = kmer_analysis_count(h, seq, qual, offsets, n_reads, on_device))) return finish(rc);
+  PartWindows w;
+  w.codes = h->codes; w.rcodes = h->rcodes; w.inv = h->inv; w.hq = h->hq;
+  w.q0 = 0; w.q1 = h->q_used;
+  const unsigned n_parts = params->n_parts > 1 ? params->n_parts : 1;
+  const unsigned part = params->n_parts > 1 ? params->part : 0;
+  if ((e = launch_hll(w, params->k, params->canonical, n_parts, part, p, d_regs, h->status, h->stream,
+                      h->num_sms)) != cudaSuccess)
+    return finish(cuda_fail(e, "hll_kernel"));
+  if ((e = cudaMemcpyAsync(regs32.data(), d_regs, m * 4, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+    return finish(cuda_fail(e, "sketch registers out"));
+  if ((rc = read_status(h))) return finish(rc);
+  if ((rc = flags_to_code(h->host_status->flags))) return finish(rc);
+  std::vector<uint8_t> regs8(m);
+  for (u64 j = 0; j < m; ++j) regs8[j] = (uint8_t)regs32[j];
+  if (registers) std::memcpy(registers, regs8.data(), m);
+  est->precision = p;
+  est->distinct = hll_estimate(regs8.data(), p);
+  est->rel_std_error = 1.04 / std::sqrt((double)m);
+  est->valid_windows = h->host_status->valid_windows;
+  return finish(KMA_OK);
 }
 
 void kmer_analysis_destroy(kma_handle* h) {

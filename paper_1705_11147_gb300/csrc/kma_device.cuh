@@ -256,6 +256,97 @@ __device__ __forceinline__ bool load_window(const PassDesc& D, u64 q, Window& w)
   return load_window(D.codes, D.rcodes, D.inv, D.hq, D.k, D.canonical, q, w);
 }
 
+// Consecutive windows starting at q (a multiple of 8), one at a time: the state
+// holds the forward k-mer F and its reverse complement R of the current window, the next
+// bases to enter (MSB first), and the invalid / high-quality bits around the windows.
+struct RollingWindows {
+  u64 fhi, flo, rhi, rlo;  // F and R as 2k-bit numbers (first base most / least significant)
+  u64 nxt;                 // bases q + k, q + k + 1, ... (MSB first)
+  u64 iv0, iv1;            // invalid bits from q (MSB first), 128 of them
+  u64 hl, hr;              // hq bits from q - 1 (left extensions) and from q + k (right)
+  unsigned left;           // base at q - 1 (left extension of window q)
+  unsigned k;
+
+  __device__ __forceinline__ void init(const PartWindows& W, unsigned kk, u64 q) {
+    k = kk;
+    const u64 v = q >> 6;
+    const unsigned t = (unsigned)(q & 63);
+    const u64 i0 = W.inv[v], i1 = W.inv[v + 1], i2 = W.inv[v + 2];
+    iv0 = fshl(i0, i1, t);
+    iv1 = fshl(i1, i2, t);
+    const u64 h0 = W.hq[v];
+    if (q > 0) {
+      const u64 vl = (q - 1) >> 6;
+      hl = fshl(W.hq[vl], W.hq[vl + 1], (unsigned)((q - 1) & 63));
+      left = code_at(W.codes, q - 1);
+    } else {
+      hl = h0 >> 1;  // no position before the arena: unusable
+      left = 0;
+    }
+    const u64 qr = q + k, vr = qr >> 6;
+    hr = fshl(W.hq[vr], W.hq[vr + 1], (unsigned)(qr & 63));
+    const u64 wr = qr >> 5;
+    nxt = fshl(W.codes[wr], W.codes[wr + 1], 2 * (unsigned)(qr & 31));
+    // window q itself, as in load_window
+    const u64 wi = q >> 5;
+    const unsigned sh2 = 2 * (unsigned)(q & 31);
+    const u64 a = W.codes[wi], b = W.codes[wi + 1];
+    const u64 top = fshl(a, b, sh2);
+    const u64 r0 = W.rcodes[wi], r1 = W.rcodes[wi + 1];
+    const u64 bot = fshr(r0, r1, sh2);
+    if (k > 32) {
+      const u64 mid = fshl(b, W.codes[wi + 2], sh2);
+      const unsigned sh = 128 - 2 * k;
+      flo = (mid >> sh) | (top << (64 - sh));
+      fhi = top >> sh;
+      rlo = bot;
+      rhi = fshr(r1, W.rcodes[wi + 2], sh2) & ((1ull << (2 * k - 64)) - 1);
+    } else {
+      flo = top >> (64 - 2 * k);
+      fhi = 0;
+      rlo = k == 32 ? bot : bot & ((1ull << (2 * k)) - 1);
+      rhi = 0;
+    }
+  }
+
+  // Window j of the run (the state holds window j): valid flag and the canonical window.
+  __device__ __forceinline__ bool get(unsigned j, unsigned canonical, Window& w) const {
+    const u64 bad = (j ? (iv0 << j) | (iv1 >> (64 - j)) : iv0) >> (64 - k);
+    if (bad) return false;
+    const unsigned ab = (unsigned)(nxt >> 62);              // base q + j + k
+    const bool au = (hr >> (63 - j)) & 1u;
+    const bool bu = (hl >> (63 - j)) & 1u;                 // base q + j - 1
+    const bool forward = !canonical || (fhi < rhi) || (fhi == rhi && flo <= rlo);
+    if (forward) {
+      w.lo = flo; w.hi = fhi;
+      w.lb = left; w.lu = bu;
+      w.rb = ab; w.ru = au;
+    } else {
+      w.lo = rlo; w.hi = rhi;
+      w.lb = 3u - ab; w.lu = au;
+      w.rb = 3u - left; w.ru = bu;
+    }
+    return true;
+  }
+
+  // Move to the next window: the base at q + j + k enters, the first base leaves.
+  __device__ __forceinline__ void roll() {
+    const unsigned b = (unsigned)(nxt >> 62);
+    nxt <<= 2;
+    if (k > 32) {
+      left = (unsigned)(fhi >> (2 * k - 66)) & 3u;
+      fhi = ((fhi << 2) | (flo >> 62)) & ((1ull << (2 * k - 64)) - 1);
+      flo = (flo << 2) | b;
+      rlo = (rlo >> 2) | (rhi << 62);
+      rhi = (rhi >> 2) | ((u64)(3u - b) << (2 * k - 66));
+    } else {
+      left = (unsigned)(flo >> (2 * k - 2)) & 3u;
+      flo = ((flo << 2) | b) & (k == 32 ? ~0ull : ((1ull << (2 * k)) - 1));
+      rlo = (rlo >> 2) | ((u64)(3u - b) << (2 * k - 2));
+    }
+  }
+};
+
 // ------------------------------------------------------------------ table
 
 __device__ __forceinline__ void cas128(Slot* s, u64 cmp_lo, u64 cmp_hi, u64 new_lo, u64 new_hi,

@@ -205,6 +205,10 @@ cudaError_t launch_part_pass(const PartGeom& g, const PartRecords& r, unsigned m
 // Key filter of the recount: set by every key in the table (after the Bloom pass).
 cudaError_t launch_keyfilter_build(const PartGeom& g, cudaStream_t stream, int num_sms);
 
+// HyperLogLog registers (2^p, 32-bit each) of the windows [w.q0, w.q1) (kma_hll.cu).
+cudaError_t launch_hll(const PartWindows& w, unsigned k, unsigned canonical, unsigned n_parts, unsigned part,
+                       unsigned p, unsigned* regs, DevStatus* st, cudaStream_t stream, int num_sms);
+
 struct LaunchShape {
   int block_threads;
   int windows_per_thread;

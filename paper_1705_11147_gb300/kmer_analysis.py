@@ -344,3 +344,51 @@ def count_kmers(seq, qual, offsets, k: int, min_depth: int = 2, min_ext_count: i
         finally:
             ka.destroy()
     raise AssertionError("unreachable")
+
+
+@dataclass
+class Estimate:
+    """HyperLogLog estimate of the distinct canonical k-mers of a read set (Section 5.1)."""
+    distinct: float
+    rel_std_error: float
+    valid_windows: int
+    precision: int
+    registers: np.ndarray  # uint8[2^precision]; merge sketches by np.maximum
+
+
+def estimate_distinct(seq, qual, offsets, k: int, canonical: bool = True, precision: int = 14,
+                      registers: np.ndarray | None = None, n_parts: int = 1, part: int = 0,
+                      stream=None, **kw) -> Estimate:
+    """One HyperLogLog pass over the reads (kmer_analysis_estimate). `registers` (optional) is
+    a sketch to merge with; the returned sketch includes it."""
+    lib = capi.load()
+    on_dev = _is_cuda_tensor(seq)
+    n_reads = int(offsets.shape[0] - 1) if not on_dev else int(offsets.numel() - 1)
+    n_bases = int(seq.numel()) if on_dev else int(offsets[-1] - offsets[0])
+    p = make_params(k=k, max_bases=max(n_bases, 1), max_reads=max(n_reads, 1), canonical=canonical,
+                    use_bloom=False, n_parts=n_parts, part=part, **kw)
+    regs = np.zeros(1 << precision, np.uint8) if registers is None else \
+        np.ascontiguousarray(registers, dtype=np.uint8).copy()
+    if regs.shape != (1 << precision,):
+        raise ValueError("registers must hold 2^precision bytes")
+    est = capi.kma_estimate(precision=precision)
+    if on_dev:
+        args = (seq.data_ptr(), qual.data_ptr(), offsets.data_ptr(), n_reads, 1)
+    else:
+        seq = np.ascontiguousarray(seq, dtype=np.uint8)
+        qual = np.ascontiguousarray(qual, dtype=np.uint8)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        args = (seq.ctypes.data, qual.ctypes.data, offsets.ctypes.data, n_reads, 0)
+    check(lib.kmer_analysis_estimate(ctypes.byref(p), *args, _stream_handle(stream), ctypes.byref(est),
+                                     regs.ctypes.data), "estimate")
+    return Estimate(float(est.distinct), float(est.rel_std_error), int(est.valid_windows),
+                    int(est.precision), regs)
+
+
+def hll_estimate(registers: np.ndarray, precision: int) -> float:
+    """Estimate of a (merged) sketch, on the host (kmer_analysis_hll_estimate)."""
+    lib = capi.load()
+    regs = np.ascontiguousarray(registers, dtype=np.uint8)
+    out = ctypes.c_double()
+    check(lib.kmer_analysis_hll_estimate(regs.ctypes.data, precision, ctypes.byref(out)), "hll_estimate")
+    return float(out.value)

@@ -169,3 +169,22 @@ def test_missing_library_fails_loudly(tmp_path):
             capi.load(str(tmp_path / "nope.so"))
     finally:
         capi._LIB = saved
+
+
+def test_hll_host_estimate_matches_oracle(lib):
+    """kmer_analysis_hll_estimate (the library's host-side estimator, no GPU) against the
+    oracle's estimator on the same sketches: empty, linear-counting range, raw range."""
+    import oracle
+    from paper_1705_11147_gb300 import capi, hll_estimate
+    rng = np.random.default_rng(5)
+    for n, p in ((0, 14), (1, 14), (3000, 14), (200_000, 14), (200_000, 8), (5000, 4)):
+        keys = np.stack([rng.integers(0, 2**63, n, dtype=np.uint64),
+                         rng.integers(0, 2**38, n, dtype=np.uint64)], 1)
+        regs = oracle.hll_registers(keys, p)
+        want = oracle.hll_estimate(regs, p)
+        got = hll_estimate(regs, p)
+        assert got == pytest.approx(want, rel=1e-12, abs=1e-12), (n, p, got, want)
+    out = ctypes.c_double()
+    r = np.zeros(1 << 14, np.uint8)
+    assert lib.kmer_analysis_hll_estimate(r.ctypes.data, 3, ctypes.byref(out)) == capi.KMA_EINVAL
+    assert lib.kmer_analysis_hll_estimate(r.ctypes.data, 15, ctypes.byref(out)) == capi.KMA_EINVAL

@@ -368,3 +368,53 @@ def test_large_200m_sampled_partition(gpu):
     want = oracle.run_readset(rs, part=part, n_parts=n_parts)
     assert_same(sub.sorted(), want, "large_200m partition 0/256")
     assert got.valid_windows == want.valid_windows
+
+
+# ------------------------------------------------------------------ HyperLogLog sizing pass
+
+def _distinct_keys(rs, k, canonical=True):
+    """All distinct keys of the read set (the oracle with min_depth 1)."""
+    return oracle.run(rs.seq, rs.qual, rs.offsets, k=k, min_depth=1, canonical=canonical,
+                      min_ext_count=2, qual_threshold=20)
+
+
+@pytest.mark.parametrize("k,canonical,p", [(31, True, 14), (21, False, 12), (51, True, 14), (63, True, 10),
+                                           (5, True, 4)])
+def test_hll_registers_match_oracle(gpu, k, canonical, p):
+    """The GPU sketch equals the oracle's sketch of the exact distinct set, register by
+    register; the estimate is within 4 relative standard errors of the exact count."""
+    from paper_1705_11147_gb300 import estimate_distinct, hll_estimate
+    rs = synth.random_reads(seed=500 + k, n_reads=6000, min_len=0, max_len=250,
+                            alphabet=b"ACGTACGTACGTACGTacgtNRY", q_lo=10, q_hi=30)
+    want = _distinct_keys(rs, k, canonical)
+    est = estimate_distinct(rs.seq, rs.qual, rs.offsets, k=k, canonical=canonical, precision=p)
+    ref = oracle.hll_registers(want.keys, p)
+    assert np.array_equal(est.registers, ref), np.nonzero(est.registers != ref)[0][:10]
+    assert est.valid_windows == want.valid_windows
+    assert est.distinct == pytest.approx(oracle.hll_estimate(ref, p), rel=1e-12)
+    assert est.distinct == pytest.approx(hll_estimate(est.registers, p), rel=1e-12)
+    n = len(want)
+    assert abs(est.distinct - n) <= 4 * est.rel_std_error * n + 2, (est.distinct, n)
+
+
+def test_hll_plain_1m_device_host_and_merge(gpu, plain):
+    """Same sketch from host and device inputs; sketches of two halves merge (elementwise
+    maximum) into the sketch of the whole; owner partitions of three 'GPUs' merge likewise."""
+    from paper_1705_11147_gb300 import estimate_distinct
+    rs, want = plain
+    k = rs.meta["params"]["k"]
+    allkeys = _distinct_keys(rs, k)
+    full = estimate_distinct(rs.seq, rs.qual, rs.offsets, k=k)
+    assert np.array_equal(full.registers, oracle.hll_registers(allkeys.keys, 14))
+    seq, qual, offs = to_dev(gpu, rs)
+    dev = estimate_distinct(seq, qual, offs, k=k)
+    assert np.array_equal(dev.registers, full.registers) and dev.valid_windows == full.valid_windows
+    half = rs.n_reads // 2
+    a = estimate_distinct(rs.seq, rs.qual, rs.offsets[:half + 1], k=k)
+    b = estimate_distinct(rs.seq, rs.qual, rs.offsets[half:], k=k, registers=a.registers)
+    assert np.array_equal(b.registers, full.registers)
+    assert a.valid_windows + b.valid_windows == full.valid_windows
+    parts = [estimate_distinct(rs.seq, rs.qual, rs.offsets, k=k, n_parts=3, part=i) for i in range(3)]
+    assert np.array_equal(np.maximum.reduce([e.registers for e in parts]), full.registers)
+    assert sum(e.valid_windows for e in parts) == full.valid_windows
+    assert abs(full.distinct - len(allkeys)) < 4 * full.rel_std_error * len(allkeys)

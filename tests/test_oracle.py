@@ -8,6 +8,7 @@
   partition independence, extension sums;
 - a statistical check of the Section 2 coverage formula f = d (1 - (k-1)/L).
 """
+import math
 import os
 import re
 from collections import Counter
@@ -285,3 +286,58 @@ def test_coverage_formula_peak():
     assert abs(mode - f) <= 2.0, (mode, f)
     mean = float(res.counts[res.counts >= 8].mean())
     assert abs(mean - f) / f < 0.05, (mean, f)
+
+
+# ---- HyperLogLog sketch (Section 5.1's cardinality pass) -----------------------------------
+
+def _random_keys(n, seed, k=51):
+    rng = np.random.default_rng(seed)
+    hi_bits = max(2 * k - 64, 1)
+    return np.stack([rng.integers(0, 2**63, n, dtype=np.uint64) * np.uint64(2)
+                     + rng.integers(0, 2, n, dtype=np.uint64),
+                     rng.integers(0, 2**hi_bits, n, dtype=np.uint64)], 1)
+
+
+def test_hll_empty_and_single():
+    # no key: every register empty, linear counting gives exactly 0
+    for p in (4, 10, 14):
+        r = oracle.hll_registers(np.zeros((0, 2), np.uint64), p)
+        assert not r.any() and oracle.hll_estimate(r, p) == 0.0
+    # one key: one register set; linear counting m ln(m / (m - 1)) = 1 + O(1/m)
+    r = oracle.hll_registers(_random_keys(1, 7), 14)
+    assert (r > 0).sum() == 1
+    assert abs(oracle.hll_estimate(r, 14) - 1.0) < 1e-3
+
+
+@pytest.mark.parametrize("n,p", [(1000, 14), (50_000, 12), (50_000, 14), (400_000, 14), (400_000, 10)])
+def test_hll_error_bound(n, p):
+    """Distinct random keys: the estimate is within 4 relative standard errors (1.04/sqrt(m),
+    Section 5.1 / Flajolet et al.) of the true count, in the linear-counting and the raw range."""
+    keys = _random_keys(n, 1000 + n + p)
+    est = oracle.hll_estimate(oracle.hll_registers(keys, p), p)
+    assert abs(est - n) / n < 4 * 1.04 / math.sqrt(2**p), (est, n)
+
+
+def test_hll_duplicates_and_merge():
+    a, b = _random_keys(20_000, 11), _random_keys(30_000, 12)
+    ra, rb = oracle.hll_registers(a, 14), oracle.hll_registers(b, 14)
+    # repeated keys change nothing: the sketch is a function of the distinct set
+    assert np.array_equal(oracle.hll_registers(np.concatenate([a, a[::3]]), 14), ra)
+    # union sketch = elementwise maximum (how sketches of read batches or GPUs merge)
+    assert np.array_equal(oracle.hll_registers(np.concatenate([a, b]), 14), np.maximum(ra, rb))
+
+
+def test_hll_rank_distribution():
+    """Ranks are geometric: with n keys in one register class, a register reaches rank >= r
+    with probability 1 - (1 - 2^-(r-1))^(n/m). Checked on the fraction of empty registers and
+    of registers at rank 1 only (the two ends a shifted or reversed rank would break)."""
+    p, n = 12, 8192
+    m = 2**p
+    r = oracle.hll_registers(_random_keys(n, 21), p)
+    lam = n / m
+    empty = (r == 0).mean()
+    assert abs(empty - math.exp(-lam)) < 0.02
+    # a register stays at rank 1 iff all its keys have rank 1 (prob 1/2 each)
+    only1 = (r == 1).mean()
+    want = sum(math.exp(-lam) * lam**j / math.factorial(j) * 0.5**j for j in range(1, 40))
+    assert abs(only1 - want) < 0.02
