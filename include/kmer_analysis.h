@@ -320,6 +320,24 @@ int kmer_analysis_estimate(const kma_params* params, const char* seq, const char
  * with 64-bit hashes no large-range correction). KMA_EINVAL on a bad precision. */
 int kmer_analysis_hll_estimate(const uint8_t* registers, uint32_t precision, double* distinct);
 
+/* ---- FASTQ parsing on the device (the input side of the stage, Section 2 item 1) ---------
+ * Splits FASTQ text into the read layout kmer_analysis_count takes. A record is four lines:
+ * "@name", the bases, "+" (optionally followed by the name) and one quality character per
+ * base; records are found by line number, so quality lines may start with '@' or '+'. Lines
+ * may end in "\n" or "\r\n"; the last line need not end in a newline; empty lines after the
+ * last record are ignored. Multi-line (wrapped) records are not supported.
+ * `text` is host memory, or device memory with on_device = 1. The outputs are device arrays
+ * owned by the caller: seq[cap_bases], qual[cap_bases] (bases and qualities of read r at
+ * [offsets[r], offsets[r+1])) and offsets[cap_reads + 1] (offsets[0] = 0). *n_reads and
+ * *n_bases (host) receive the sizes, also when they exceed the capacities (then KMA_EFULL
+ * is returned and the arrays are incomplete). Temporaries come from the library's pool.
+ * Synchronises `cuda_stream`. Errors: KMA_EINVAL (a record without '@' or '+' line, or whose
+ * base and quality lines differ in length; a line count that is not a multiple of four),
+ * KMA_EFULL, KMA_ENOMEM, KMA_ECUDA. */
+int kmer_analysis_parse_fastq(const char* text, uint64_t n_bytes, int on_device, char* seq, char* qual,
+                              uint64_t* offsets, uint64_t cap_bases, uint64_t cap_reads, uint64_t* n_reads,
+                              uint64_t* n_bases, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

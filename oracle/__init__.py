@@ -181,3 +181,30 @@ def hll_estimate(registers: np.ndarray, precision: int) -> float:
     r = np.ascontiguousarray(registers, dtype=np.uint8)
     assert r.shape == (1 << precision,)
     return float(_lib().oracle_hll_estimate(r.ctypes.data, precision))
+
+
+def parse_fastq(text: bytes):
+    """FASTQ text -> (seq, qual, offsets) numpy arrays, record by record in plain Python (small
+    inputs only). A record is four lines: '@' name, bases, '+' line, qualities of the same
+    length; '\r' before '\n' is dropped; the last line may lack '\n'; empty lines after the
+    last record are ignored. Raises ValueError on anything else."""
+    lines = text.split(b"\n")
+    if lines and lines[-1] == b"":
+        lines.pop()  # the text ended with a newline
+    lines = [ln[:-1] if ln.endswith(b"\r") else ln for ln in lines]
+    while len(lines) % 4 and lines and lines[-1] == b"":
+        lines.pop()
+    if len(lines) % 4:
+        raise ValueError("line count is not a multiple of four")
+    seqs, quals = [], []
+    for r in range(len(lines) // 4):
+        head, bases, plus, q = lines[4 * r: 4 * r + 4]
+        if not head.startswith(b"@") or not plus.startswith(b"+") or len(bases) != len(q):
+            raise ValueError(f"record {r} is malformed")
+        seqs.append(bases)
+        quals.append(q)
+    seq = np.frombuffer(b"".join(seqs), dtype=np.uint8).copy()
+    qual = np.frombuffer(b"".join(quals), dtype=np.uint8).copy()
+    offs = np.zeros(len(seqs) + 1, np.uint64)
+    offs[1:] = np.cumsum([len(s) for s in seqs]) if seqs else []
+    return seq, qual, offs

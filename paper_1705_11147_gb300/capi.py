@@ -96,6 +96,8 @@ _SIGS = {
     "kmer_analysis_estimate": ([ctypes.POINTER(kma_params), vp, vp, vp, u64, ctypes.c_int, vp,
                                 ctypes.POINTER(kma_estimate), vp], ctypes.c_int),
     "kmer_analysis_hll_estimate": ([vp, u32, ctypes.POINTER(dbl)], ctypes.c_int),
+    "kmer_analysis_parse_fastq": ([vp, u64, ctypes.c_int, vp, vp, vp, u64, u64, ctypes.POINTER(u64),
+                                   ctypes.POINTER(u64), vp], ctypes.c_int),
 }
 
 _LIB = None

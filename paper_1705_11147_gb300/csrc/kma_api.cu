@@ -1147,6 +1147,112 @@ int kmer_analysis_estimate(const kma_params* params, const char* seq, const char
   return finish(KMA_OK);
 }
 
+int kmer_analysis_parse_fastq(const char* text, uint64_t n_bytes, int on_device, char* seq, char* qual,
+                              uint64_t* offsets, uint64_t cap_bases, uint64_t cap_reads, uint64_t* n_reads,
+                              uint64_t* n_bases, void* cuda_stream) {
+  if (!n_reads || !n_bases || !offsets || (n_bytes && !text)) return KMA_EINVAL;
+  *n_reads = *n_bases = 0;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, rc;
+  KMA_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  if ((rc = get_pool(dev, &pool))) return rc;
+  std::vector<void*> temps;
+  auto alloc = [&](void** p, u64 bytes) -> int {
+    cudaError_t e = cudaMallocFromPoolAsync(p, std::max<u64>(bytes, 8), pool, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? KMA_ENOMEM : cuda_fail(e, "fastq temporaries");
+    }
+    temps.push_back(*p);
+    return KMA_OK;
+  };
+  auto done = [&](int code) {
+    for (void* p : temps) cudaFreeAsync(p, st);
+    cudaStreamSynchronize(st);
+    return code;
+  };
+#define FQ_CUDA(call)                                              \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return done(cuda_fail(e_, #call));      \
+  } while (0)
+  if (n_bytes == 0) {
+    FQ_CUDA(cudaMemsetAsync(offsets, 0, 8, st));
+    return done(KMA_OK);
+  }
+  const unsigned char* d_text = (const unsigned char*)text;
+  if (!on_device) {
+    void* t = nullptr;
+    if ((rc = alloc(&t, n_bytes))) return done(rc);
+    FQ_CUDA(cudaMemcpyAsync(t, text, n_bytes, cudaMemcpyHostToDevice, st));
+    d_text = (const unsigned char*)t;
+  }
+  // 1-2: newlines per chunk, scanned (one extra element receives the total)
+  const u64 chunks = fastq_chunks(n_bytes);
+  u64 *cc = nullptr, *tmp = nullptr;
+  if ((rc = alloc((void**)&cc, (chunks + 1) * 8)) ||
+      (rc = alloc((void**)&tmp, scan_scratch_items(std::max<u64>(chunks + 1, 1)) * 8)))
+    return done(rc);
+  FQ_CUDA(launch_fastq_count(d_text, n_bytes, cc, st));
+  FQ_CUDA(cudaMemsetAsync(cc + chunks, 0, 8, st));
+  FQ_CUDA(scan_exclusive(cc, chunks + 1, tmp, st));
+  u64 n_lines = 0;
+  FQ_CUDA(cudaMemcpyAsync(&n_lines, cc + chunks, 8, cudaMemcpyDeviceToHost, st));
+  FQ_CUDA(cudaStreamSynchronize(st));
+  // 3: line ends
+  u64* line_end = nullptr;
+  if ((rc = alloc((void**)&line_end, n_lines * 8))) return done(rc);
+  FQ_CUDA(launch_fastq_lines(d_text, n_bytes, cc, line_end, st));
+  // lines after the last complete record must be empty
+  const u64 extra = n_lines % 4;
+  if (extra) {
+    const u64 first = n_lines - extra;  // first extra line
+    u64 ends[4] = {0, 0, 0, 0};
+    const u64 from = first ? first - 1 : 0, cnt = first ? extra + 1 : extra;
+    FQ_CUDA(cudaMemcpyAsync(ends, line_end + from, cnt * 8, cudaMemcpyDeviceToHost, st));
+    FQ_CUDA(cudaStreamSynchronize(st));
+    u64 prev_end = first ? ends[0] : (u64)-1;  // (u64)-1 + 1 == 0: the text's first byte
+    for (u64 i = 0; i < extra; ++i) {
+      const u64 e = ends[first ? i + 1 : i];
+      const u64 len = e - (prev_end + 1);
+      if (len > 1) return done(KMA_EINVAL);
+      if (len == 1) {  // a lone '\r' is an empty line too
+        char c = 0;
+        FQ_CUDA(cudaMemcpyAsync(&c, d_text + prev_end + 1, 1, cudaMemcpyDeviceToHost, st));
+        FQ_CUDA(cudaStreamSynchronize(st));
+        if (c != '\r') return done(KMA_EINVAL);
+      }
+      prev_end = e;
+    }
+  }
+  const u64 nr = (n_lines - extra) / 4;
+  *n_reads = nr;
+  if (nr > cap_reads) return done(KMA_EFULL);
+  // 4-5: record checks, bases per record, scanned into the offsets
+  unsigned long long* bad = nullptr;
+  if ((rc = alloc((void**)&bad, 8))) return done(rc);
+  u64* scan_tmp = nullptr;
+  if ((rc = alloc((void**)&scan_tmp, scan_scratch_items(nr + 1) * 8))) return done(rc);
+  FQ_CUDA(cudaMemsetAsync(bad, 0xFF, 8, st));
+  FQ_CUDA(launch_fastq_records(d_text, line_end, nr, (u64*)offsets, bad, st));
+  FQ_CUDA(cudaMemsetAsync(offsets + nr, 0, 8, st));
+  FQ_CUDA(scan_exclusive((u64*)offsets, nr + 1, scan_tmp, st));
+  u64 back[2] = {0, 0};
+  FQ_CUDA(cudaMemcpyAsync(&back[0], offsets + nr, 8, cudaMemcpyDeviceToHost, st));
+  FQ_CUDA(cudaMemcpyAsync(&back[1], bad, 8, cudaMemcpyDeviceToHost, st));
+  FQ_CUDA(cudaStreamSynchronize(st));
+  if (back[1] != ~0ull) return done(KMA_EINVAL);
+  *n_bases = back[0];
+  if (back[0] > cap_bases) return done(KMA_EFULL);
+  if (nr && (!seq || !qual)) return done(KMA_EINVAL);
+  // 6: bases and qualities
+  FQ_CUDA(launch_fastq_copy(d_text, line_end, nr, (const u64*)offsets, (unsigned char*)seq,
+                            (unsigned char*)qual, st));
+  return done(KMA_OK);
+#undef FQ_CUDA
+}
+
 void kmer_analysis_destroy(kma_handle* h) {
   if (!h) return;
   free_all(h);

@@ -205,6 +205,23 @@ cudaError_t launch_part_pass(const PartGeom& g, const PartRecords& r, unsigned m
 // Key filter of the recount: set by every key in the table (after the Bloom pass).
 cudaError_t launch_keyfilter_build(const PartGeom& g, cudaStream_t stream, int num_sms);
 
+// FASTQ parsing (kma_fastq.cu) and the device-wide exclusive scan it uses.
+unsigned long long scan_scratch_items(unsigned long long n);
+cudaError_t scan_exclusive(unsigned long long* data, unsigned long long n, unsigned long long* tmp,
+                           cudaStream_t stream);
+unsigned long long fastq_chunks(unsigned long long n_bytes);
+cudaError_t launch_fastq_count(const unsigned char* text, unsigned long long n, unsigned long long* chunk_counts,
+                               cudaStream_t stream);
+cudaError_t launch_fastq_lines(const unsigned char* text, unsigned long long n,
+                               const unsigned long long* chunk_offsets, unsigned long long* line_end,
+                               cudaStream_t stream);
+cudaError_t launch_fastq_records(const unsigned char* text, const unsigned long long* line_end,
+                                 unsigned long long n_reads, unsigned long long* seq_len,
+                                 unsigned long long* bad, cudaStream_t stream);
+cudaError_t launch_fastq_copy(const unsigned char* text, const unsigned long long* line_end,
+                              unsigned long long n_reads, const unsigned long long* offsets, unsigned char* seq,
+                              unsigned char* qual, cudaStream_t stream);
+
 // HyperLogLog registers (2^p, 32-bit each) of the windows [w.q0, w.q1) (kma_hll.cu).
 cudaError_t launch_hll(const PartWindows& w, unsigned k, unsigned canonical, unsigned n_parts, unsigned part,
                        unsigned p, unsigned* regs, DevStatus* st, cudaStream_t stream, int num_sms);

@@ -392,3 +392,29 @@ def hll_estimate(registers: np.ndarray, precision: int) -> float:
     out = ctypes.c_double()
     check(lib.kmer_analysis_hll_estimate(regs.ctypes.data, precision, ctypes.byref(out)), "hll_estimate")
     return float(out.value)
+
+
+def parse_fastq(text, stream=None):
+    """FASTQ text (bytes / numpy uint8 on the host, or a torch uint8 CUDA tensor) -> (seq, qual,
+    offsets) as torch CUDA tensors (uint8, uint8, int64), ready for KmerAnalysis.count
+    (kmer_analysis_parse_fastq). Capacities are bounded from the text size (a record takes at
+    least six bytes and two per base), so one call suffices."""
+    torch = _torch()
+    lib = capi.load()
+    if _is_cuda_tensor(text):
+        ptr, n, on_dev = text.data_ptr(), int(text.numel()), 1
+        keep = text
+    else:
+        keep = np.frombuffer(text, dtype=np.uint8) if isinstance(text, (bytes, bytearray)) else \
+            np.ascontiguousarray(text, dtype=np.uint8)
+        ptr, n, on_dev = keep.ctypes.data, int(keep.shape[0]), 0
+    cap_bases, cap_reads = n // 2 + 1, n // 6 + 1
+    seq = torch.empty(cap_bases, dtype=torch.uint8, device="cuda")
+    qual = torch.empty(cap_bases, dtype=torch.uint8, device="cuda")
+    offs = torch.empty(cap_reads + 1, dtype=torch.int64, device="cuda")
+    nr, nb = ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib.kmer_analysis_parse_fastq(ptr, n, on_dev, seq.data_ptr(), qual.data_ptr(), offs.data_ptr(),
+                                        cap_bases, cap_reads, ctypes.byref(nr), ctypes.byref(nb),
+                                        _stream_handle(stream)), "parse_fastq")
+    del keep
+    return seq[:nb.value], qual[:nb.value], offs[:nr.value + 1]

@@ -3,6 +3,8 @@
 Every comparison is bit-exact (integer work): same k-mer set, counts, eight extension
 counters and two side codes per k-mer, after sorting both by key (record order is
 unspecified on the GPU)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -418,3 +420,66 @@ def test_hll_plain_1m_device_host_and_merge(gpu, plain):
     assert np.array_equal(np.maximum.reduce([e.registers for e in parts]), full.registers)
     assert sum(e.valid_windows for e in parts) == full.valid_windows
     assert abs(full.distinct - len(allkeys)) < 4 * full.rel_std_error * len(allkeys)
+
+
+# ------------------------------------------------------------------ FASTQ parsing on the device
+
+def _to_fastq(rs, crlf=False, final_newline=True):
+    nl = b"\r\n" if crlf else b"\n"
+    out = []
+    for r in range(rs.n_reads):
+        a, b = int(rs.offsets[r]), int(rs.offsets[r + 1])
+        out += [b"@read%d" % r, rs.seq[a:b].tobytes(), b"+", rs.qual[a:b].tobytes()]
+    text = nl.join(out)
+    return text + nl if final_newline else text
+
+
+def _parse_gpu(gpu, text, device=False):
+    from paper_1705_11147_gb300 import parse_fastq
+    if device:
+        text = gpu.from_numpy(np.frombuffer(text, np.uint8).copy()).cuda()
+    seq, qual, offs = parse_fastq(text)
+    return seq.cpu().numpy(), qual.cpu().numpy(), offs.cpu().numpy().astype(np.uint64)
+
+
+@pytest.mark.parametrize("crlf,final_newline,device", [(False, True, False), (True, True, True),
+                                                       (False, False, True), (True, False, False)])
+def test_fastq_parse_matches_oracle(gpu, crlf, final_newline, device):
+    """Synthetic reads (empty and short reads, N/IUPAC/lowercase bases, qualities over the whole
+    printable range, so quality lines start with '@' or '+') written as FASTQ: the device
+    parser returns the reads exactly, as does the oracle's parser."""
+    rs = synth.random_reads(seed=31, n_reads=5000, min_len=0, max_len=300,
+                            alphabet=b"ACGTACGTACGTacgtNRY", q_lo=0, q_hi=60)
+    text = _to_fastq(rs, crlf, final_newline)
+    got = _parse_gpu(gpu, text, device)
+    want = oracle.parse_fastq(text)
+    for a, b, c in zip(got, want, (rs.seq, rs.qual, rs.offsets - rs.offsets[0])):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_fastq_golden_and_errors(gpu):
+    from paper_1705_11147_gb300 import capi
+    text = open(os.path.join(os.path.dirname(__file__), "golden", "fastq_records.fastq"), "rb").read()
+    for t in (text, text + b"\n\n\r\n"):
+        got, want = _parse_gpu(gpu, t), oracle.parse_fastq(t)
+        assert all(np.array_equal(a, b) for a, b in zip(got, want))
+    for bad in (b"@a\nAC\n-\nII\n", b"@a\nAC\n+\nI\n", b"@a\nAC\n+\nII\nX\n", b"a\nAC\n+\nII\n"):
+        with pytest.raises(capi.KmaError) as e:
+            _parse_gpu(gpu, bad)
+        assert e.value.code == capi.KMA_EINVAL
+    assert [len(x) for x in _parse_gpu(gpu, b"")] == [0, 0, 1]
+
+
+def test_fastq_parse_then_count(gpu, plain):
+    """FASTQ text of the 30 Mbase workload -> device parser -> counting: the same records as the
+    oracle on the original reads."""
+    from paper_1705_11147_gb300 import KmerAnalysis, make_params, parse_fastq
+    rs, want = plain
+    seq, qual, offs = parse_fastq(_to_fastq(rs))
+    p = dict(rs.meta["params"])
+    p.pop("bloom_fpr", None)
+    with KmerAnalysis(make_params(max_bases=rs.n_bases, max_reads=rs.n_reads, expected_distinct=rs.n_bases,
+                                  **p)) as ka:
+        ka.count(seq, qual, offs)
+        ka.finalize()
+        assert_same(ka.copy_result().sorted(), want, "fastq")

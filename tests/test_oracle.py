@@ -341,3 +341,26 @@ def test_hll_rank_distribution():
     only1 = (r == 1).mean()
     want = sum(math.exp(-lam) * lam**j / math.factorial(j) * 0.5**j for j in range(1, 40))
     assert abs(only1 - want) < 0.02
+
+
+
+# ---- FASTQ parsing (input side of the stage) ------------------------------------------------
+
+def test_fastq_golden_records():
+    text = open(os.path.join(GOLD, "fastq_records.fastq"), "rb").read()
+    want = [ln.split() for ln in open(os.path.join(GOLD, "fastq_records_expected.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    seq, qual, offs = oracle.parse_fastq(text)
+    assert len(offs) == len(want) + 1
+    for r, (b, q) in enumerate(want):
+        b, q = ("" if b == "-" else b), ("" if q == "-" else q)
+        assert bytes(seq[offs[r]:offs[r + 1]]).decode() == b
+        assert bytes(qual[offs[r]:offs[r + 1]]).decode() == q
+    # trailing empty lines change nothing; a missing '+' or a length mismatch is an error
+    assert all(np.array_equal(a, b) for a, b in zip(oracle.parse_fastq(text + b"\n\n\r\n"), (seq, qual, offs)))
+    with pytest.raises(ValueError):
+        oracle.parse_fastq(b"@a\nAC\n-\nII\n")
+    with pytest.raises(ValueError):
+        oracle.parse_fastq(b"@a\nAC\n+\nI\n")
+    with pytest.raises(ValueError):
+        oracle.parse_fastq(b"@a\nAC\n+\nII\nX\n")
