@@ -392,6 +392,16 @@ def run_ours(args, ws, rank, local):
               "recipe_expected_distinct": int(prm.expected_distinct),
               "what": "HyperLogLog pass (pack + sketch, temporary arena), host wall time"}
 
+    # Section 5.2's next stage on the finalized result, timed once (not part of the step)
+    torch.cuda.synchronize(dev)
+    t_cg = time.perf_counter()
+    cg = capi.kma_contigs()
+    capi.check(capi.load().kmer_analysis_contigs(ka.handle, ctypes.byref(cg)), "contigs")
+    t_cg = time.perf_counter() - t_cg
+    contigs = {"ms": round(t_cg * 1e3, 1), "n_contigs": int(cg.n_contigs), "n_bases": int(cg.n_bases),
+               "n_vertices": int(cg.n_vertices), "n_cycles": int(cg.n_cycles),
+               "what": "contig generation on the finalized k-mers (list ranking), host wall time"}
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, ka, rs, dev, qkeys, ws)
@@ -414,7 +424,7 @@ def run_ours(args, ws, rank, local):
            "tuning": {k2: getattr(prm, k2) for k2 in ("block_threads", "windows_per_thread", "ctas_per_sm",
                                                       "warp_aggregate", "slot_prefetch", "partitions")}
                      | {"partitions_used": int(plan_used.partitions)},
-           "clocks": clk, "generation_s": round(t_gen, 1), "sizing_pass": sizing}
+           "clocks": clk, "generation_s": round(t_gen, 1), "sizing_pass": sizing, "contigs": contigs}
     if e2e:
         out["e2e"] = e2e
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -556,7 +566,7 @@ def run_batched(args, ws, rank, local):
             "plain": {"value": round(plain_value, 3), "unit": UNIT, "ms_per_step": round(ms_plain, 2),
                       "path": "create -> count -> finalize -> destroy per sample"},
             "batched_vs_plain": round(value / plain_value, 3), "gpu_launches": int(launches),
-            "clocks": clk, "generation_s": round(t_gen, 1), "sizing_pass": sizing}
+            "clocks": clk, "generation_s": round(t_gen, 1), "sizing_pass": sizing, "contigs": contigs}
 
 
 # ------------------------------------------------------------------ served (job stream)

@@ -47,8 +47,9 @@ extern "C" {
                               the read-packing kernel) gave up: no partial result */
 #define KMA_EOVERFLOW (-6) /* a 32-bit k-mer counter would have wrapped */
 #define KMA_ECUDA (-7)     /* a CUDA runtime call failed (cudaGetLastError text via strerror) */
-#define KMA_ETOOLARGE (-8) /* input larger than the fixed scratch of the allocation-free entry
-                              point (KMA_NOALLOC_MAX_BASES / KMA_NOALLOC_MAX_READS) */
+#define KMA_ETOOLARGE (-8) /* input above a fixed limit: the allocation-free entry point's
+                              scratch (KMA_NOALLOC_MAX_BASES / KMA_NOALLOC_MAX_READS), or
+                              2^31 contig-graph vertices */
 
 #define KMA_CODE_X 4
 #define KMA_CODE_F 5
@@ -283,6 +284,32 @@ int kmer_analysis_count_small_noalloc(const kma_params* params, const char* seq,
                                       uint64_t* keys, uint32_t* counts, uint32_t* ext,
                                       uint8_t* codes, uint64_t capacity, uint64_t* n_out,
                                       void* cuda_stream);
+
+/* ---- Contig generation (Section 5.2) on a finalized handle --------------------------------
+ * Vertices: the finalized k-mers without a fork on either side (codes A/C/G/T or X; Section 2
+ * removes the fork vertices). The neighbour of k-mer x on its right is x[1..k) + R, on its
+ * left L + x[0..k-1) (R, L: its side codes; X: no neighbour), looked up by key; it is an edge
+ * only if it is another vertex whose code on the facing side points back to x. Contigs are
+ * the resulting paths, k-mers merged (length = k-mers + k - 1); a cycle is cut at its
+ * smallest key, on that k-mer's left side. Contigs are in unspecified order, each in one of
+ * its two orientations (with forward keys: read forward). */
+typedef struct {
+  uint64_t n_contigs;
+  uint64_t n_bases;        /* total length */
+  uint64_t n_vertices;     /* k-mers in the graph (no fork on either side) */
+  uint64_t n_cycles;       /* circular components that were cut */
+  const char* seq;         /* device: contig bases (A, C, G, T), concatenated */
+  const uint64_t* offsets; /* device: [n_contigs + 1]; contig i is seq[offsets[i] .. offsets[i+1]) */
+} kma_contigs;
+
+/* Build the contigs of the finalized result; the arrays are owned by the handle (valid until
+ * the next kmer_analysis_contigs, reset or destroy). Synchronises. Errors: KMA_ESTATE (not
+ * finalized), KMA_ENOMEM, KMA_ETOOLARGE (2^31 or more vertices), KMA_ECUDA. */
+int kmer_analysis_contigs(kma_handle* h, kma_contigs* out);
+
+/* Copy the contigs to caller buffers (n_bases bytes, n_contigs + 1 offsets; host or device per
+ * on_device; NULL skips an array). Synchronises. KMA_ESTATE before kmer_analysis_contigs. */
+int kmer_analysis_copy_contigs(kma_handle* h, char* seq, uint64_t* offsets, int on_device);
 
 /* ---- Cardinality estimate (Section 5.1: a HyperLogLog pass sizes the Bloom filter) --------
  * Estimates the number of distinct canonical k-mers of a read set with a HyperLogLog sketch

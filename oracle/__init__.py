@@ -53,6 +53,13 @@ def _lib():
         lib.oracle_hll_registers.argtypes = [p, u64, u32, p]
         lib.oracle_hll_estimate.argtypes = [p, u32]
         lib.oracle_hll_estimate.restype = ctypes.c_double
+        lib.oracle_contigs.argtypes = [p, p, u64, u32, ctypes.c_int]
+        lib.oracle_contigs.restype = p
+        for fn in ("oracle_contigs_n", "oracle_contigs_bases", "oracle_contigs_cycles"):
+            getattr(lib, fn).argtypes = [p]
+            getattr(lib, fn).restype = u64
+        lib.oracle_contigs_fetch.argtypes = [p, p, p]
+        lib.oracle_contigs_free.argtypes = [p]
         _LIB = lib
     return _LIB
 
@@ -208,3 +215,21 @@ def parse_fastq(text: bytes):
     offs = np.zeros(len(seqs) + 1, np.uint64)
     offs[1:] = np.cumsum([len(s) for s in seqs]) if seqs else []
     return seq, qual, offs
+
+
+def contigs(keys: np.ndarray, codes: np.ndarray, k: int, canonical: bool = True):
+    """Contigs (Section 5.2) of a k-mer analysis result, walked k-mer by k-mer: a list of
+    strings (each in the orientation its walk took) and the number of cycles that were cut."""
+    q = np.ascontiguousarray(keys, dtype=np.uint64).reshape(-1, 2)
+    c = np.ascontiguousarray(codes, dtype=np.uint8).reshape(-1, 2)
+    lib = _lib()
+    h = lib.oracle_contigs(q.ctypes.data, c.ctypes.data, q.shape[0], k, int(canonical))
+    try:
+        n, nb = lib.oracle_contigs_n(h), lib.oracle_contigs_bases(h)
+        buf = ctypes.create_string_buffer(nb + 1)
+        offs = np.zeros(n + 1, np.uint64)
+        lib.oracle_contigs_fetch(h, buf, offs.ctypes.data)
+        raw = buf.raw[:nb].decode()
+        return [raw[int(offs[i]):int(offs[i + 1])] for i in range(n)], int(lib.oracle_contigs_cycles(h))
+    finally:
+        lib.oracle_contigs_free(h)

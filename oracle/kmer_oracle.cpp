@@ -378,6 +378,30 @@ void oracle_unpack_keys(const uint64_t* keys, uint64_t n, uint32_t k, char* out)
   }
 }
 
+// ---- Contig generation (Section 5.2), walked one k-mer at a time ------------------------
+// Vertices: the k-mers of a k-mer analysis result without a fork on either side (Section 2
+// excludes the vertices with non-unique neighbours; a side code X means no neighbour there,
+// as in the two-letter codes of Section 4.1). The right neighbour of a k-mer x (in the
+// orientation of its key) is y = x[1..k) + R, R its right extension; the left neighbour is
+// L + x[0..k-1). The neighbour is looked up by its key (with canonical keys: the smaller of y
+// and its reverse complement). Reading taken here (Section 5.2 extends a subcontig while the
+// lookup succeeds): the step is taken only if the neighbour is a vertex whose own extension
+// on the facing side points back to x (mutual), and never from a k-mer to itself. Components
+// are then simple paths or cycles; a contig is a path's k-mers merged (length = k-mers + k - 1).
+// A cycle is cut at its smallest key, on that k-mer's left side, and becomes a path.
+
+struct ContigResult {
+  std::string bases;
+  std::vector<uint64_t> offsets{0};
+  uint64_t cycles = 0;
+};
+
+std::string canonical_of(const std::string& w, int canonical) {
+  if (!canonical) return w;
+  std::string rc = reverse_complement(w);
+  return rc < w ? rc : w;
+}
+
 // ---- HyperLogLog sketch (Section 5.1's cardinality pass), from its definition ----------
 // The sketch of a set of distinct keys with m = 2^p registers: each key (lo, hi) is hashed to
 // 64 bits by the sketch's hash h = fmix64(lo XOR (hi * 0x9e3779b97f4a7c15 + 0x632be59bd9b4e019)),
@@ -433,5 +457,104 @@ double oracle_hll_estimate(const uint8_t* regs, uint32_t p) {
   if (e <= 2.5 * md && zeros > 0) return md * std::log(md / (double)zeros);
   return e;
 }
+
+void* oracle_contigs(const uint64_t* keys, const uint8_t* codes, uint64_t n, uint32_t k, int canonical) {
+  auto* res = new ContigResult();
+  std::vector<std::string> str;
+  std::vector<int> lc, rc;
+  std::unordered_map<std::string, int64_t> index;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (codes[2 * i] == 5 || codes[2 * i + 1] == 5) continue;  // a fork on either side
+    index[unpack(Key{keys[2 * i], keys[2 * i + 1]}, k)] = (int64_t)str.size();
+    str.push_back(unpack(Key{keys[2 * i], keys[2 * i + 1]}, k));
+    lc.push_back(codes[2 * i]);
+    rc.push_back(codes[2 * i + 1]);
+  }
+  const int64_t m = (int64_t)str.size();
+  // adj[u][side] = (v, side of v it enters), side 0 = left, 1 = right; v = -1: none
+  std::vector<std::array<std::pair<int64_t, int>, 2>> adj(m);
+  for (int64_t u = 0; u < m; ++u) {
+    const std::string& x = str[u];
+    for (int side = 0; side < 2; ++side) {
+      adj[u][side] = {-1, 0};
+      if ((side ? rc[u] : lc[u]) == 4) continue;  // X: no neighbour on this side
+      const std::string y = side ? x.substr(1) + "ACGT"[rc[u]] : std::string(1, "ACGT"[lc[u]]) + x.substr(0, k - 1);
+      const std::string key = canonical_of(y, canonical);
+      auto it = index.find(key);
+      if (it == index.end() || it->second == u) continue;
+      const int64_t v = it->second;
+      const bool same = key == y;  // v read in the orientation of its key
+      int enter;
+      bool mutual;
+      if (side == 1) {  // leaving x to the right: x[0] must be v's extension on the facing side
+        enter = same ? 0 : 1;
+        mutual = same ? lc[v] == code_of(x[0]) : rc[v] == code_of(complement(x[0]));
+      } else {          // leaving x to the left: x[k-1] must be v's extension on the facing side
+        enter = same ? 1 : 0;
+        mutual = same ? rc[v] == code_of(x[k - 1]) : lc[v] == code_of(complement(x[k - 1]));
+      }
+      if (mutual) adj[u][side] = {v, enter};
+    }
+  }
+  std::vector<char> seen(m, 0);
+  for (int64_t u0 = 0; u0 < m; ++u0) {
+    if (seen[u0]) continue;
+    // the component of u0
+    std::vector<int64_t> comp{u0};
+    seen[u0] = 1;
+    for (size_t i = 0; i < comp.size(); ++i)
+      for (int side = 0; side < 2; ++side) {
+        const int64_t v = adj[comp[i]][side].first;
+        if (v >= 0 && !seen[v]) seen[v] = 1, comp.push_back(v);
+      }
+    // an end of the path: one with a free left side if there is one (forward keys: the start)
+    int64_t end = -1;
+    for (int64_t v : comp)
+      if (adj[v][0].first < 0) { end = v; break; }
+    if (end < 0)
+      for (int64_t v : comp)
+        if (adj[v][1].first < 0) { end = v; break; }
+    if (end < 0) {  // a cycle: cut it at the smallest key, on that k-mer's left side
+      int64_t mn = comp[0];
+      for (int64_t v : comp)
+        if (str[v] < str[mn]) mn = v;
+      const auto [w, t] = adj[mn][0];
+      adj[w][t] = {-1, 0};
+      adj[mn][0] = {-1, 0};
+      end = mn;
+      ++res->cycles;
+    }
+    // walk from the end: forward if its left side is free, else in reverse
+    bool fwd = adj[end][0].first < 0;
+    std::string contig = fwd ? str[end] : reverse_complement(str[end]);
+    int64_t cur = end;
+    int exit = fwd ? 1 : 0;
+    while (true) {
+      const auto [v, t] = adj[cur][exit];
+      if (v < 0) break;
+      if (t == 0) {  // entered v on its left: v read forward
+        contig.push_back(str[v][k - 1]);
+        exit = 1;
+      } else {
+        contig.push_back(complement(str[v][0]));
+        exit = 0;
+      }
+      cur = v;
+    }
+    res->bases += contig;
+    res->offsets.push_back(res->bases.size());
+  }
+  return res;
+}
+
+uint64_t oracle_contigs_n(void* h) { return ((ContigResult*)h)->offsets.size() - 1; }
+uint64_t oracle_contigs_bases(void* h) { return ((ContigResult*)h)->bases.size(); }
+uint64_t oracle_contigs_cycles(void* h) { return ((ContigResult*)h)->cycles; }
+void oracle_contigs_fetch(void* h, char* bases, uint64_t* offsets) {
+  auto* r = (ContigResult*)h;
+  std::memcpy(bases, r->bases.data(), r->bases.size());
+  std::memcpy(offsets, r->offsets.data(), r->offsets.size() * 8);
+}
+void oracle_contigs_free(void* h) { delete (ContigResult*)h; }
 
 }  // extern "C"

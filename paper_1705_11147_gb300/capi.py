@@ -59,6 +59,11 @@ class kma_timings(ctypes.Structure):
 KERNEL_KINDS = ("pack", "pass", "recount", "classify", "query", "init", "unused", "scatter")
 
 
+class kma_contigs(ctypes.Structure):
+    _fields_ = [("n_contigs", u64), ("n_bases", u64), ("n_vertices", u64), ("n_cycles", u64),
+                ("seq", vp), ("offsets", vp)]
+
+
 class kma_estimate(ctypes.Structure):
     _fields_ = [("precision", u32), ("pad", u32), ("distinct", dbl), ("rel_std_error", dbl),
                 ("valid_windows", u64)]
@@ -96,6 +101,8 @@ _SIGS = {
     "kmer_analysis_estimate": ([ctypes.POINTER(kma_params), vp, vp, vp, u64, ctypes.c_int, vp,
                                 ctypes.POINTER(kma_estimate), vp], ctypes.c_int),
     "kmer_analysis_hll_estimate": ([vp, u32, ctypes.POINTER(dbl)], ctypes.c_int),
+    "kmer_analysis_contigs": ([vp, ctypes.POINTER(kma_contigs)], ctypes.c_int),
+    "kmer_analysis_copy_contigs": ([vp, vp, vp, ctypes.c_int], ctypes.c_int),
     "kmer_analysis_parse_fastq": ([vp, u64, ctypes.c_int, vp, vp, vp, u64, u64, ctypes.POINTER(u64),
                                    ctypes.POINTER(u64), vp], ctypes.c_int),
 }

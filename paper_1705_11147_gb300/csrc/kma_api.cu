@@ -257,6 +257,10 @@ struct kma_handle {
   struct RecBatch { void* keys; unsigned char* info; u64* fill; u64 cap, ocap; };
   std::vector<RecBatch> rec_batches;
 
+  // contigs of the finalized result (kmer_analysis_contigs), freed by reset / destroy
+  char* contig_seq = nullptr;
+  u64* contig_offsets = nullptr;
+  u64 contig_n = 0, contig_bases = 0, contig_vertices = 0, contig_cycles = 0;
   u64* out_keys = nullptr;
   unsigned* out_counts = nullptr;
   unsigned* out_ext = nullptr;
@@ -335,12 +339,21 @@ void free_records(kma_handle* h) {
   h->rec_batches.clear();
 }
 
+void free_contigs(kma_handle* h) {
+  if (h->contig_seq) cudaFreeAsync(h->contig_seq, h->stream);
+  if (h->contig_offsets) cudaFreeAsync(h->contig_offsets, h->stream);
+  h->contig_seq = nullptr;
+  h->contig_offsets = nullptr;
+  h->contig_n = h->contig_bases = h->contig_vertices = h->contig_cycles = 0;
+}
+
 void free_all(kma_handle* h) {
   free_records(h);
   dfree(h, h->codes); dfree(h, h->rcodes); dfree(h, h->inv); dfree(h, h->hq); dfree(h, h->marks);
   dfree(h, h->bloom); dfree(h, h->keyfilter); dfree(h, h->table); dfree(h, h->status);
   for (int i = 0; i < 2; ++i) { dfree(h, h->stage_seq[i]); dfree(h, h->stage_qual[i]); dfree(h, h->stage_offs[i]); }
   dfree(h, h->out_keys); dfree(h, h->out_counts); dfree(h, h->out_ext); dfree(h, h->out_codes);
+  free_contigs(h);
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->host_status) cudaFreeHost(h->host_status);
   h->host_status = nullptr;
@@ -359,6 +372,7 @@ void free_all(kma_handle* h) {
 
 int clear_state(kma_handle* h) {
   free_records(h);
+  free_contigs(h);
   KMA_CUDA(cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->stream));
   if (h->bloom) KMA_CUDA(cudaMemsetAsync(h->bloom, 0, h->d.plan.bloom_words * 8, h->stream));
   if (h->keyfilter) KMA_CUDA(cudaMemsetAsync(h->keyfilter, 0, h->d.Wt * h->d.P * 8, h->stream));
@@ -1063,6 +1077,38 @@ int kmer_analysis_timings(kma_handle* h, kma_timings* out, int reset) {
   return KMA_OK;
 }
 
+int kmer_analysis_contigs(kma_handle* h, kma_contigs* out) {
+  if (!h || !out) return KMA_EINVAL;
+  if (!h->finalized) return KMA_ESTATE;
+  free_contigs(h);
+  cudaError_t err = cudaSuccess;
+  const int rc = contig_pass(h->out_keys, h->out_codes, h->res.n, h->p.k, h->p.canonical, h->pool, h->stream,
+                             &h->contig_seq, &h->contig_offsets, &h->contig_n, &h->contig_bases,
+                             &h->contig_vertices, &h->contig_cycles, &h->status->flags, &err);
+  if (rc == KMA_ECUDA) return cuda_fail(err, "contig generation");
+  if (rc) return rc;
+  int st = read_status(h);
+  if (st) return st;
+  if (h->host_status->flags & kFlagFull) return KMA_EFULL;
+  out->n_contigs = h->contig_n;
+  out->n_bases = h->contig_bases;
+  out->n_vertices = h->contig_vertices;
+  out->n_cycles = h->contig_cycles;
+  out->seq = h->contig_seq;
+  out->offsets = (const uint64_t*)h->contig_offsets;
+  return KMA_OK;
+}
+
+int kmer_analysis_copy_contigs(kma_handle* h, char* seq, uint64_t* offsets, int on_device) {
+  if (!h) return KMA_EINVAL;
+  if (!h->contig_offsets) return KMA_ESTATE;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (seq && h->contig_bases) KMA_CUDA(cudaMemcpyAsync(seq, h->contig_seq, h->contig_bases, kind, h->stream));
+  if (offsets) KMA_CUDA(cudaMemcpyAsync(offsets, h->contig_offsets, (h->contig_n + 1) * 8, kind, h->stream));
+  KMA_CUDA(cudaStreamSynchronize(h->stream));
+  return KMA_OK;
+}
+
 int kmer_analysis_hll_estimate(const uint8_t* registers, uint32_t precision, double* distinct) {
   if (!registers || !distinct || precision < KMA_HLL_MIN_PRECISION || precision > KMA_HLL_MAX_PRECISION)
     return KMA_EINVAL;
@@ -1269,7 +1315,7 @@ const char* kmer_analysis_strerror(int code) {
     case KMA_ETIMEOUT: return "device wait timed out";
     case KMA_EOVERFLOW: return "k-mer counter overflow";
     case KMA_ECUDA: return g_last_cuda_error.empty() ? "CUDA error" : g_last_cuda_error.c_str();
-    case KMA_ETOOLARGE: return "input exceeds the allocation-free entry point's fixed scratch limits";
+    case KMA_ETOOLARGE: return "input exceeds a fixed limit (allocation-free scratch, or 2^31 contig vertices)";
     default: return "unknown error";
   }
 }

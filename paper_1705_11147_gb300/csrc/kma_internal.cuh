@@ -222,6 +222,13 @@ cudaError_t launch_fastq_copy(const unsigned char* text, const unsigned long lon
                               unsigned long long n_reads, const unsigned long long* offsets, unsigned char* seq,
                               unsigned char* qual, cudaStream_t stream);
 
+// Contig generation over finalized records (kma_contig.cu). Returns 0, a negative KMA_E*
+// code (-7 = CUDA error in *err), and on success pool allocations in *seq_out / *offsets_out.
+int contig_pass(const unsigned long long* keys, const unsigned char* codes, unsigned long long n, unsigned k,
+                unsigned canonical, cudaMemPool_t pool, cudaStream_t st, char** seq_out,
+                unsigned long long** offsets_out, unsigned long long* n_contigs, unsigned long long* n_bases,
+                unsigned long long* n_vertices, unsigned long long* n_cycles, unsigned* dev_flags, cudaError_t* err);
+
 // HyperLogLog registers (2^p, 32-bit each) of the windows [w.q0, w.q1) (kma_hll.cu).
 cudaError_t launch_hll(const PartWindows& w, unsigned k, unsigned canonical, unsigned n_parts, unsigned part,
                        unsigned p, unsigned* regs, DevStatus* st, cudaStream_t stream, int num_sms);

@@ -137,6 +137,20 @@ class KmerAnalysis:
               "copy_result")
         return Result(keys, counts, ext, codes, int(r.n_uu), int(r.valid_windows), int(r.table_keys))
 
+    def contigs(self):
+        """Contigs of the finalized result (kmer_analysis_contigs, Section 5.2): (list of
+        strings, info) with info = {n_contigs, n_bases, n_vertices, n_cycles}."""
+        c = capi.kma_contigs()
+        check(self._lib.kmer_analysis_contigs(self._h, ctypes.byref(c)), "contigs")
+        seq = np.zeros(max(int(c.n_bases), 1), np.uint8)
+        offs = np.zeros(int(c.n_contigs) + 1, np.uint64)
+        check(self._lib.kmer_analysis_copy_contigs(self._h, seq.ctypes.data, offs.ctypes.data, 0), "copy_contigs")
+        raw = seq[:int(c.n_bases)].tobytes().decode()
+        strings = [raw[int(offs[i]):int(offs[i + 1])] for i in range(int(c.n_contigs))]
+        info = {"n_contigs": int(c.n_contigs), "n_bases": int(c.n_bases), "n_vertices": int(c.n_vertices),
+                "n_cycles": int(c.n_cycles)}
+        return strings, info
+
     def copy_result_device(self):
         """Result arrays as torch CUDA tensors (copies of the handle-owned buffers)."""
         torch = _torch()

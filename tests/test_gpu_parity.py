@@ -483,3 +483,78 @@ def test_fastq_parse_then_count(gpu, plain):
         ka.count(seq, qual, offs)
         ka.finalize()
         assert_same(ka.copy_result().sorted(), want, "fastq")
+
+
+# ------------------------------------------------------------------ contig generation
+
+def _rc(s):
+    return s.translate(str.maketrans("ACGT", "TGCA"))[::-1]
+
+
+def _canon_sorted(contigs, canonical=True):
+    return sorted(min(c, _rc(c)) for c in contigs) if canonical else sorted(contigs)
+
+
+def _gpu_contigs(gpu, rs, **params):
+    from paper_1705_11147_gb300 import KmerAnalysis, make_params
+    p = dict(params)
+    p.setdefault("max_bases", max(rs.n_bases, 1))
+    p.setdefault("max_reads", max(rs.n_reads, 1))
+    p.setdefault("expected_distinct", max(rs.n_bases, 1))
+    with KmerAnalysis(make_params(**p)) as ka:
+        ka.count(rs.seq, rs.qual, rs.offsets)
+        ka.finalize()
+        res = ka.copy_result()
+        strings, info = ka.contigs()
+        return strings, info, res
+
+
+def _check_contigs(gpu, rs, k, canonical=True, min_depth=2, min_ext_count=2, **gpu_only):
+    want_res = oracle.run(rs.seq, rs.qual, rs.offsets, k=k, min_depth=min_depth, min_ext_count=min_ext_count,
+                          canonical=canonical, qual_threshold=20)
+    want, want_cycles = oracle.contigs(want_res.keys, want_res.codes, k, canonical)
+    gpu_only.setdefault("use_bloom", min_depth >= 2)  # the Bloom pass drops singletons
+    got, info, _ = _gpu_contigs(gpu, rs, k=k, min_depth=min_depth, min_ext_count=min_ext_count,
+                                canonical=canonical, qual_threshold=20, **gpu_only)
+    assert info["n_cycles"] == want_cycles
+    assert info["n_contigs"] == len(want) and info["n_bases"] == sum(len(c) for c in want)
+    assert _canon_sorted(got, canonical) == _canon_sorted(want, canonical)
+    return got, info
+
+
+def test_contigs_golden_examples(gpu):
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "contigs_examples.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        reads, want = (x.strip() for x in line.split("|"))
+        rs = readset(reads.split(","))
+        got, info, _ = _gpu_contigs(gpu, rs, k=3, min_depth=2, min_ext_count=2, canonical=False, use_bloom=False)
+        assert sorted(got) == want.split(","), (reads, got)
+
+
+def test_contigs_linear_and_circular_genomes(gpu):
+    rng = np.random.default_rng(9)
+    g = "".join("ACGT"[i] for i in rng.integers(0, 4, 5000))
+    for circular in (False, True):
+        gg = g + g if circular else g
+        reads = []
+        for i in range(0, len(g) if circular else len(g) - 119, 6):
+            reads += [gg[i:i + 120], _rc(gg[i:i + 120])]
+        if not circular:
+            reads += [g[-120:], _rc(g[-120:])]
+        got, info = _check_contigs(gpu, readset(reads), 31)
+        assert info["n_contigs"] == 1 and info["n_cycles"] == int(circular)
+        assert len(got[0]) == len(g) + (30 if circular else 0)
+
+
+@pytest.mark.parametrize("k,canonical", [(31, True), (21, False), (51, True)])
+def test_contigs_random_reads(gpu, k, canonical):
+    rs = synth.random_reads(seed=70 + k, n_reads=20000, min_len=60, max_len=200, alphabet=b"ACGT", q_lo=15, q_hi=40)
+    _check_contigs(gpu, rs, k, canonical=canonical, min_depth=1, min_ext_count=1)
+
+
+def test_contigs_plain_and_bacterial(gpu, plain):
+    rs, _ = plain
+    _check_contigs(gpu, rs, rs.meta["params"]["k"])
+    rb = synth.workload("bacterial_5m", scale=0.2)
+    _check_contigs(gpu, rb, rb.meta["params"]["k"], partitions=4)

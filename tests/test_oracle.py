@@ -364,3 +364,76 @@ def test_fastq_golden_records():
         oracle.parse_fastq(b"@a\nAC\n+\nI\n")
     with pytest.raises(ValueError):
         oracle.parse_fastq(b"@a\nAC\n+\nII\nX\n")
+
+
+# ---- Contig generation (Section 5.2) --------------------------------------------------------
+
+def _revcomp(s):
+    return s.translate(str.maketrans("ACGT", "TGCA"))[::-1]
+
+
+def _contigs_of(reads, k, canonical, min_depth=1, min_ext=1):
+    seq, qual, offs = oracle.reads_from_strings(reads)
+    r = oracle.run(seq, qual, offs, k=k, min_depth=min_depth, min_ext_count=min_ext, canonical=canonical)
+    got, cycles = oracle.contigs(r.keys, r.codes, k, canonical)
+    return got, cycles, r
+
+
+def test_contig_golden_examples():
+    for line in open(os.path.join(GOLD, "contigs_examples.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        reads, want = (x.strip() for x in line.split("|"))
+        got, cycles, _ = _contigs_of(reads.split(","), 3, canonical=False, min_depth=2, min_ext=2)
+        assert sorted(got) == want.split(",") and cycles == 0, (reads, got)
+
+
+def _genome(n, seed):
+    rng = np.random.default_rng(seed)
+    return "".join("ACGT"[i] for i in rng.integers(0, 4, n))
+
+
+def test_contig_linear_genome_is_one_contig():
+    """Error-free reads from both strands tiling a random genome: one contig, the genome
+    itself in one orientation."""
+    g, k, L = _genome(3000, 5), 31, 120
+    reads = []
+    for i in range(0, len(g) - L + 1, 7):
+        reads += [g[i:i + L], _revcomp(g[i:i + L])]
+    reads += [g[-L:], _revcomp(g[-L:])]
+    got, cycles, _ = _contigs_of(reads, k, canonical=True, min_depth=2)
+    assert cycles == 0 and len(got) == 1 and got[0] in (g, _revcomp(g))
+
+
+def test_contig_circular_genome_is_cut_cycle():
+    """Reads around a circular genome: one cycle, cut at its smallest k-mer (left side), so
+    the contig starts with that k-mer and is the whole circle plus k - 1 bases."""
+    g, k, L = _genome(2000, 6), 31, 100
+    gg = g + g
+    reads = []
+    for i in range(0, len(g), 5):
+        reads += [gg[i:i + L], _revcomp(gg[i:i + L])]
+    got, cycles, r = _contigs_of(reads, k, canonical=True, min_depth=2)
+    assert cycles == 1 and len(got) == 1
+    c = got[0]
+    assert len(c) == len(g) + k - 1 and c[-(k - 1):] == c[:k - 1]
+    assert c[:len(g)] in gg or c[:len(g)] in _revcomp(g) * 2      # a rotation, either strand
+    kmers = [gg[i:i + k] for i in range(len(g))]
+    smallest = min(min(x, _revcomp(x)) for x in kmers)
+    # cut on the smallest k-mer's left side: it is an end of the contig, read forward from it
+    assert c.startswith(smallest) or c.endswith(_revcomp(smallest))
+
+
+def test_contig_vertices_used_once():
+    """Synthetic reads with errors and repeats: every vertex (no fork on either side) lies in
+    exactly one contig, and every k-mer of every contig is a vertex."""
+    rs = synth.workload("plain_1m", scale=0.05)
+    r = oracle.run(rs.seq, rs.qual, rs.offsets, k=31, min_depth=2, min_ext_count=2, canonical=True)
+    got, cycles = oracle.contigs(r.keys, r.codes, 31, True)
+    vertices = set(oracle.unpack(r.keys[(r.codes[:, 0] != 5) & (r.codes[:, 1] != 5)], 31))
+    seen = []
+    for c in got:
+        for i in range(len(c) - 30):
+            w = c[i:i + 31]
+            seen.append(min(w, _revcomp(w)))
+    assert len(seen) == len(set(seen)) == len(vertices) and set(seen) == vertices
