@@ -379,9 +379,14 @@ def run_ours(args, ws, rank, local):
     kernel_ms = {k2[3:]: round(v / args.steps, 3) for k2, v in timing.items() if k2.startswith("ms_")}
     launches = int(timing["launches"])
 
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, ka, rs, dev, qkeys, ws)
+
     # Section 5.1's cardinality pass, timed once on the resident reads (not part of the step:
     # the step is sized from the workload recipe, as a user who knows the genome would)
-    from paper_1705_11147_gb300 import estimate_distinct
+    import ctypes
+    from paper_1705_11147_gb300 import capi, estimate_distinct
     estimate_distinct(seq, qual, offs, k=k, canonical=bool(prm.canonical), stream=stream)  # warm
     torch.cuda.synchronize(dev)
     t_est = time.perf_counter()
@@ -392,7 +397,8 @@ def run_ours(args, ws, rank, local):
               "recipe_expected_distinct": int(prm.expected_distinct),
               "what": "HyperLogLog pass (pack + sketch, temporary arena), host wall time"}
 
-    # Section 5.2's next stage on the finalized result, timed once (not part of the step)
+    # Section 5.2's next stage on the finalized result, timed once after the
+    # measured steps (not part of the step; its temporaries do not share the pool with them)
     torch.cuda.synchronize(dev)
     t_cg = time.perf_counter()
     cg = capi.kma_contigs()
@@ -402,9 +408,7 @@ def run_ours(args, ws, rank, local):
                "n_vertices": int(cg.n_vertices), "n_cycles": int(cg.n_cycles),
                "what": "contig generation on the finalized k-mers (list ranking), host wall time"}
 
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(args, ka, rs, dev, qkeys, ws)
+
     ka.destroy()
     del seq, qual, offs
 
