@@ -19,12 +19,12 @@
 //     have Phred quality >= qual_threshold. When the key is the reverse complement of w, the
 //     sides swap and the bases are complemented.
 //  5. Error filter (Section 2 item 1, Section 5.1): keep keys with count >= min_depth
-//     (the paper keeps k-mers occurring "more than epsilon" times: min_depth = epsilon + 1).
+//     (the paper keeps k-mers seen more than epsilon times: min_depth = epsilon + 1).
 //  6. High-quality extensions (Section 5.1, threshold t_hq): on each side the set
 //     H = {b : ext[b] >= min_ext_count}. The side code is b if |H| = 1, X (no neighbour,
 //     Section 4.1) if |H| = 0 and F (fork, excluded from contigs, Section 2) if |H| >= 2.
 //     Unique-extension (UU, Section 5.2) k-mers have A/C/G/T on both sides.
-//  7. Owner-computes partitioning (Section 5.1, "necessary and sufficient"): with n_parts > 1
+//  7. Owner-computes partitioning (Section 5.1: a fixed k-mer -> owner map): with n_parts > 1
 //     only keys with fnv1a(key string) mod n_parts == part are kept; the union over all parts
 //     equals the whole result. The FNV-1a hash here is the oracle's own.
 //
