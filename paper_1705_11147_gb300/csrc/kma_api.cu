@@ -483,6 +483,67 @@ PartGeom part_geom(kma_handle* h) {
 // bases) on stream `st`. One table: Bloom test-and-set (or counting) in place. Partitions:
 // scatter into per-partition record buckets, then the record pass part by part; the buckets
 // are kept for the recount in finalize. Nothing here waits for the GPU.
+// Partitioned mode: record buckets for a count() call of n_pos arena positions (n_reads reads,
+// n_bases bases), appended to the handle's record batches (kept for the recount).
+int prepare_records(kma_handle* h, u64 n_pos, u64 n_reads, u64 n_bases, cudaStream_t st, size_t& index) {
+  const u64 P = h->d.P, k = h->p.k;
+  // Bucket capacity from the window count of reads of length >= k (exact for such reads);
+  // shorter reads, hash imbalance and repeated k-mers spill into the overflow area. Both are
+  // multiples of 16 records (the record passes stage 16-byte aligned tiles).
+  const u64 w_est = n_bases > (k - 1) * n_reads ? n_bases - (k - 1) * n_reads : 0;
+  u64 cap = ((u64)((double)w_est / (double)P * 1.05) + 64 + 15) & ~15ull;
+  u64 ocap = n_pos / 16 + 65536;
+  if (P * cap < n_bases) ocap = std::max(ocap, n_bases - P * cap + n_pos / 64);
+  ocap = (ocap + 15) & ~15ull;
+  if (cap >= (1ull << 32)) return KMA_EINVAL;  // more partitions needed for this batch size
+  h->count_bound += cap + ocap;
+  const u64 total = P * cap + ocap;
+  kma_handle::RecBatch rb{nullptr, nullptr, nullptr, cap, ocap};
+  const size_t kb = (size_t)total * (k > 32 ? 16 : 8);
+  cudaError_t e = cudaMallocFromPoolAsync(&rb.keys, kb, h->pool, st);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&rb.info, (size_t)total, h->pool, st);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&rb.fill, (size_t)(P + 1) * 8, h->pool, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (rb.keys) cudaFreeAsync(rb.keys, st);
+    if (rb.info) cudaFreeAsync(rb.info, st);
+    return e == cudaErrorMemoryAllocation ? KMA_ENOMEM : cuda_fail(e, "record buckets");
+  }
+  h->rec_batches.push_back(rb);
+  index = h->rec_batches.size() - 1;
+  KMA_CUDA(cudaMemsetAsync(rb.fill, 0, (size_t)(P + 1) * 8, st));
+  return KMA_OK;
+}
+
+PartRecords records_of(const kma_handle::RecBatch& rb) {
+  PartRecords r;
+  r.keys = rb.keys; r.info = rb.info; r.cap = rb.cap; r.ocap = rb.ocap; r.fill = rb.fill;
+  return r;
+}
+
+// Partitioned mode: the windows [q0, q0 + n_pos) into record batch `index`.
+int scatter_windows(kma_handle* h, size_t index, u64 q0, u64 n_pos, cudaStream_t st) {
+  const PartGeom g = part_geom(h);
+  PartWindows w;
+  w.codes = h->codes; w.rcodes = h->rcodes; w.inv = h->inv; w.hq = h->hq;
+  w.q0 = q0; w.q1 = q0 + n_pos;
+  const PartRecords r = records_of(h->rec_batches[index]);
+  return timed_launch(h, KMA_KERNEL_SCATTER, st, n_pos > 0,
+                      [&] { return launch_part_scatter(g, w, r, st, h->num_sms); });
+}
+
+// Partitioned mode: the record pass (Bloom test-and-set, or counting) over batch `index`.
+int record_pass(kma_handle* h, size_t index, cudaStream_t st) {
+  const unsigned mode = h->p.use_bloom ? kModeBloom : kModeCount;
+  const PartGeom g = part_geom(h);
+  const PartRecords r = records_of(h->rec_batches[index]);
+  return timed_launch(h, KMA_KERNEL_PASS, st, true, [&] { return launch_part_pass(g, r, mode, st, h->num_sms); });
+}
+
+// First pass over the windows [q0, q0 + n_pos) of one packed batch (n_reads reads, n_bases
+// bases) on stream `st`. One table: Bloom test-and-set (or counting) in place. Partitions:
+// scatter into per-partition record buckets, then the record pass part by part; the buckets
+// are kept for the recount in finalize. Nothing here waits for the GPU.
 int first_pass(kma_handle* h, u64 q0, u64 n_pos, u64 n_reads, u64 n_bases, cudaStream_t st) {
   const unsigned mode = h->p.use_bloom ? kModeBloom : kModeCount;
   if (h->d.P <= 1) {
@@ -498,42 +559,10 @@ int first_pass(kma_handle* h, u64 q0, u64 n_pos, u64 n_reads, u64 n_bases, cudaS
     return timed_launch(h, KMA_KERNEL_PASS, st, b.total_tiles > 0,
                         [&] { return launch_pass(b, h->shape, h->agg, st); });
   }
-  PartWindows w;
-  w.codes = h->codes; w.rcodes = h->rcodes; w.inv = h->inv; w.hq = h->hq;
-  w.q0 = q0; w.q1 = q0 + n_pos;
-  const u64 P = h->d.P, k = h->p.k;
-  // Bucket capacity from the window count of reads of length >= k (exact for such reads);
-  // shorter reads, hash imbalance and repeated k-mers spill into the overflow area. Both are
-  // multiples of 16 records (the record passes stage 16-byte aligned tiles).
-  const u64 w_est = n_bases > (k - 1) * n_reads ? n_bases - (k - 1) * n_reads : 0;
-  u64 cap = ((u64)((double)w_est / (double)P * 1.05) + 64 + 15) & ~15ull;
-  u64 ocap = n_pos / 16 + 65536;
-  if (P * cap < n_bases) ocap = std::max(ocap, n_bases - P * cap + n_pos / 64);
-  ocap = (ocap + 15) & ~15ull;
-  if (cap >= (1ull << 32)) return KMA_EINVAL;  // more partitions needed for this batch size
-  h->count_bound += cap + ocap;
-  const PartGeom g = part_geom(h);
-  const u64 total = P * cap + ocap;
-  kma_handle::RecBatch rb{nullptr, nullptr, nullptr, cap, ocap};
-  const size_t kb = (size_t)total * (k > 32 ? 16 : 8);
-  cudaError_t e = cudaMallocFromPoolAsync(&rb.keys, kb, h->pool, st);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&rb.info, (size_t)total, h->pool, st);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&rb.fill, (size_t)(P + 1) * 8, h->pool, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    if (rb.keys) cudaFreeAsync(rb.keys, st);
-    if (rb.info) cudaFreeAsync(rb.info, st);
-    return e == cudaErrorMemoryAllocation ? KMA_ENOMEM : cuda_fail(e, "record buckets");
-  }
-  h->rec_batches.push_back(rb);
-  KMA_CUDA(cudaMemsetAsync(rb.fill, 0, (size_t)(P + 1) * 8, st));
-  PartRecords r;
-  r.keys = rb.keys; r.info = rb.info; r.cap = cap; r.ocap = ocap; r.fill = rb.fill;
-  int rc = timed_launch(h, KMA_KERNEL_SCATTER, st, n_pos > 0,
-                        [&] { return launch_part_scatter(g, w, r, st, h->num_sms); });
-  if (rc) return rc;
-  return timed_launch(h, KMA_KERNEL_PASS, st, n_pos > 0,
-                      [&] { return launch_part_pass(g, r, mode, st, h->num_sms); });
+  size_t index = 0;
+  int rc = prepare_records(h, n_pos, n_reads, n_bases, st, index);
+  if (rc || (rc = scatter_windows(h, index, q0, n_pos, st))) return rc;
+  return n_pos ? record_pass(h, index, st) : KMA_OK;
 }
 
 int run_pack_and_pass(kma_handle* h, const PackDesc& pd) {
@@ -701,6 +730,19 @@ int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual, const 
     if (offsets[r + 1] < offsets[r]) return KMA_EINVAL;
   if (offsets[n_reads] - offsets[0] + h->bases_used > h->p.max_bases) return KMA_EFULL;
   if ((rc = setup_staging(h))) return rc;
+  // With partitions, every staged chunk is packed and scattered into one set of record buckets
+  // (so the copy of the next chunk overlaps both), and the record pass runs once over all of
+  // them: a pass per chunk would bring every partition's filter and table back into L2 once
+  // per chunk.
+  const bool parts = h->d.P > 1 && !h->pack_only;
+  size_t rec_index = 0;
+  if (parts) {
+    // positions of the whole call: every chunk is rounded up to 64 positions, and a chunk
+    // ends only when the next read would overflow the staged bases or read offsets
+    const u64 nb_all = offsets[n_reads] - offsets[0];
+    const u64 chunks = 2 * (nb_all / h->d.staging + n_reads / (h->stage_offs_cap - 1) + 1);
+    if ((rc = prepare_records(h, nb_all + n_reads + 64 * chunks, n_reads, nb_all, h->stream, rec_index))) return rc;
+  }
   u64 r0 = 0;
   while (r0 < n_reads) {
     u64 r1 = r0;
@@ -732,9 +774,14 @@ int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual, const 
                            [&] { return launch_pack(pb, h->stream, h->num_sms); })))
       return rc;
     KMA_CUDA(cudaEventRecord(h->consumed[b], h->stream));
-    if (!h->pack_only && (rc = first_pass(h, q0, n_pos, r1 - r0, nb, h->stream))) return rc;
+    if (parts) {
+      if ((rc = scatter_windows(h, rec_index, q0, n_pos, h->stream))) return rc;
+    } else if (!h->pack_only && (rc = first_pass(h, q0, n_pos, r1 - r0, nb, h->stream))) {
+      return rc;
+    }
     r0 = r1;
   }
+  if (parts && (rc = record_pass(h, rec_index, h->stream))) return rc;
   // Host buffers may be reused once the call returns: wait for the copies.
   KMA_CUDA(cudaStreamSynchronize(h->copy_stream));
   return KMA_OK;
