@@ -105,6 +105,13 @@ typedef struct {
                                  counted in place; P >= 2: that many parts (<= 4096 for
                                  k <= 32, <= 2048 for k > 32; more: KMA_EINVAL). Results
                                  do not depend on it. */
+  uint32_t heavy_hitters;     /* 1: k-mers with very many occurrences (satellites, low-complexity
+                                 sequence) are expected. The partitioned counting passes then
+                                 look for equal keys among each warp's records and treat them
+                                 as one (one Bloom test-and-set and one table probe per group,
+                                 counter updates summed in shared memory first: Section 5.1's
+                                 local accumulation of heavy hitters, at warp level). 0: off.
+                                 Results do not depend on it. */
 } kma_params;
 
 /* Sizes derived from a kma_params (pure host arithmetic, no GPU needed). */

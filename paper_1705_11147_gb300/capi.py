@@ -37,7 +37,8 @@ class kma_params(ctypes.Structure):
                 ("load_factor", dbl), ("staging_bytes", u64),
                 ("block_threads", u32), ("windows_per_thread", u32), ("ctas_per_sm", u32),
                 ("warp_aggregate", u32), ("n_parts", u32), ("part", u32),
-                ("slot_prefetch", u32), ("fault_inject", u32), ("partitions", u32)]
+                ("slot_prefetch", u32), ("fault_inject", u32), ("partitions", u32),
+                ("heavy_hitters", u32)]
 
 
 class kma_plan(ctypes.Structure):

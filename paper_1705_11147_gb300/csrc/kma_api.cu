@@ -120,6 +120,7 @@ int check_params(const kma_params* p) {
     return KMA_EINVAL;
   if (p->slot_prefetch > 2) return KMA_EINVAL;
   if (p->fault_inject > 1) return KMA_EINVAL;
+  if (p->heavy_hitters > 1) return KMA_EINVAL;
   if (p->partitions > (p->k > 32 ? kMaxPartitionsWide : kMaxPartitions)) return KMA_EINVAL;
   if (p->n_parts > 1 && p->part >= p->n_parts) return KMA_EINVAL;
   return KMA_OK;
@@ -476,6 +477,7 @@ PartGeom part_geom(kma_handle* h) {
   g.rpt = h->p.windows_per_thread >= 4 ? 4 : 2;
   g.wait_limit = 1u << 22;
   g.no_overflow = h->count_bound < (1ull << 32) ? 1u : 0u;
+  g.group = h->p.heavy_hitters ? 1u : 0u;
   return g;
 }
 

@@ -172,7 +172,7 @@ struct PartGeom {
   unsigned int rpt;             // records per thread in flight in the record passes (2 or 4)
   unsigned int wait_limit;      // polls of the bounded wait for a staged record tile
   unsigned int no_overflow;     // 1: no count can reach 2^32 (host bound), counts use red.add
-  unsigned int pad;
+  unsigned int group;           // 1: group equal keys within a warp (heavy hitters)
 };
 
 struct PartWindows {

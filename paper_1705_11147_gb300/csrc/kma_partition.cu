@@ -203,6 +203,8 @@ struct WarpStage {
   u64 keys[2][kTile * KW];
   unsigned char info[2][kTile];
   unsigned char list[kTile];              // recount: indices of the flagged records
+  unsigned char dup[64];                  // equal keys among a round of 32 records: a lane per hash slot
+  unsigned acc[32][10];                   // per group leader: occurrences by left / right outcome
   unsigned long long bar[2];
 };
 static_assert(sizeof(WarpStage<1, 2>) % 16 == 0 && sizeof(WarpStage<2, 2>) % 16 == 0 &&
@@ -255,7 +257,7 @@ __device__ __forceinline__ void rec_issue(WarpStage<KW, RPT>& S, const PartRecor
 
 __device__ __forceinline__ u64 shfl0(u64 v) { return __shfl_sync(0xffffffffu, v, 0); }
 
-template <int KW, int RPT, unsigned MODE>
+template <int KW, int RPT, unsigned MODE, bool GROUP>
 __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount ? 6 : 4) : 2) part_pass_kernel(const __grid_constant__ PartGeom G,
                                                                  const __grid_constant__ PartRecords R) {
   constexpr int kTile = WarpStage<KW, RPT>::kTile;
@@ -352,6 +354,35 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
         p[j] = part_of(h[j], G.P);
       }
     }
+    // Equal keys in a round of 32 records (frequent k-mers: satellites, low-complexity
+    // sequence) act as one group: only its leader does the Bloom test-and-set and the table
+    // probe, and the group's counter updates are summed in shared memory and applied once
+    // (the paper accumulates frequent k-mers locally before a global reduction, Section 5.1;
+    // here the locality is the warp). Each lane writes its lane number at a slot chosen by its
+    // hash; a lane whose slot holds another lane with the same key joins that lane's group.
+    // Only with GROUP (the heavy_hitters parameter): elsewhere every lane is its own group.
+    bool dup[RPT];
+    unsigned ldr[RPT];
+    bool anydup = false;
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+      dup[j] = false;
+      ldr[j] = lane;
+    }
+    if (GROUP && MODE != kModeRecount) {
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) {
+        const unsigned slot = (unsigned)h[j] & 63u;
+        if (act[j]) S.dup[slot] = (unsigned char)lane;
+        __syncwarp();
+        const unsigned wl = act[j] ? S.dup[slot] : lane;
+        const u64 wlo = __shfl_sync(0xffffffffu, w[j].lo, wl), whi = __shfl_sync(0xffffffffu, w[j].hi, wl);
+        dup[j] = act[j] && wl != lane && wlo == w[j].lo && whi == w[j].hi;
+        ldr[j] = dup[j] ? wl : lane;
+        anydup |= __any_sync(0xffffffffu, dup[j]);
+        __syncwarp();  // the slots are rewritten by the next round
+      }
+    }
     // stage 2: Bloom test-and-set in the partition's sub-filter; first sightings flagged
     if (MODE == kModeBloom) {
       u64 old[RPT], msk[RPT];
@@ -360,15 +391,21 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
         old[j] = msk[j] = 0;
         if (act[j]) {
           msk[j] = bloom_mask(h[j], G.bloom_h);
-          old[j] = atomicOr(G.bloom + (u64)p[j] * G.Wp + bloom_index(h[j], G.Wp), msk[j]);
+          if (!dup[j]) old[j] = atomicOr(G.bloom + (u64)p[j] * G.Wp + bloom_index(h[j], G.Wp), msk[j]);
         }
       }
 #pragma unroll
       for (int j = 0; j < RPT; ++j) {
-        const bool first = act[j] && (old[j] & msk[j]) != msk[j];
+        // a group's members come after its leader: they have been seen
+        const bool first = act[j] && !dup[j] && (old[j] & msk[j]) != msk[j];
         if (first) st_stream(R.info + base + rec[j], (unsigned)si[rec[j]] | kInfoFirst, pol);
         acc_first += __popc(__ballot_sync(0xffffffffu, first));
         act[j] = act[j] && !first;
+        // a group whose leader was the first sighting: its members resolve on their own
+        if (GROUP && __shfl_sync(0xffffffffu, first, ldr[j])) {
+          dup[j] = false;
+          ldr[j] = lane;
+        }
       }
     }
     // recount: most first sightings are of k-mers seen once, which never reached the table;
@@ -381,14 +418,14 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
         act[j] = (__ldcg(G.keyfilter + (u64)p[j] * G.Wk + keyfilter_index(h[j], G.Wk)) & m) == m;
       }
     }
-    // stage 3: first probe in the partition's sub-table
+    // stage 3: first probe in the partition's sub-table (group leaders only)
     ulonglong2 kv[RPT];
     u64 idx[RPT];
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
       kv[j] = make_ulonglong2(0, 0);
       idx[j] = 0;
-      if (act[j]) {
+      if (act[j] && (MODE == kModeRecount || !dup[j])) {
         idx[j] = table_index(h[j], G.Sp);
         kv[j] = __ldcg(reinterpret_cast<const ulonglong2*>(G.table + (u64)p[j] * G.Sp + idx[j]));
       }
@@ -398,7 +435,7 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
     for (int j = 0; j < RPT; ++j) {
       Slot* s = nullptr;
       bool inserted = false;
-      if (act[j]) {
+      if (act[j] && (MODE == kModeRecount || !dup[j])) {
         Slot* sub = G.table + (u64)p[j] * G.Sp;
         if (MODE == kModeRecount) {
           bool full;
@@ -410,7 +447,29 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
         }
       }
       if (MODE != kModeRecount) acc_ins += __popc(__ballot_sync(0xffffffffu, inserted));
-      if (s) {
+      if (GROUP && MODE != kModeRecount && anydup) {
+        // sum each group's outcomes in its leader's block, then the leader applies them
+        unsigned* blk = S.acc[lane];
+#pragma unroll
+        for (int c = 0; c < 10; ++c) blk[c] = 0;
+        __syncwarp();
+        if (act[j]) {
+          atomicAdd(&S.acc[ldr[j]][w[j].lu ? w[j].lb : 4u], 1u);
+          atomicAdd(&S.acc[ldr[j]][5u + (w[j].ru ? w[j].rb : 4u)], 1u);
+        }
+        __syncwarp();
+        if (s) {
+#pragma unroll
+          for (int c = 0; c < 10; ++c) {
+            const unsigned v = blk[c];
+            if (!v) continue;
+            unsigned* ctr = c < 4 ? &s->ext[c] : c == 4 ? &s->none[0] : c < 9 ? &s->ext[c - 1] : &s->none[1];
+            if (G.no_overflow) red_add(ctr, v);
+            else if (atomicAdd(ctr, v) > 0xFFFFFFFFu - v) atomicOr(&G.status->flags, kFlagOverflow);
+          }
+        }
+        __syncwarp();  // the blocks are cleared by the next round
+      } else if (s) {
         if (G.no_overflow) add_occurrence_red(s, w[j]);
         else add_occurrence(s, w[j], 1u, G.status);
       }
@@ -482,26 +541,32 @@ cudaError_t launch_part_scatter(const PartGeom& g, const PartWindows& w, const P
   return cudaGetLastError();
 }
 
-template <int KW, int RPT, unsigned MODE>
+template <int KW, int RPT, unsigned MODE, bool GROUP>
 static cudaError_t launch_pass_rt(const PartGeom& g, const PartRecords& r, cudaStream_t stream, int num_sms) {
   constexpr int tile = 32 * RPT;
   const u64 tiles = (u64)g.P * ((r.cap + tile - 1) / tile) + (r.ocap + tile - 1) / tile;
   if (tiles == 0) return cudaSuccess;
   if ((r.cap | r.ocap) & 15 || (reinterpret_cast<uintptr_t>(r.keys) | reinterpret_cast<uintptr_t>(r.info)) & 15)
     return cudaErrorInvalidValue;  // staging needs 16-record buckets on 16-byte boundaries
-  const void* fn = (const void*)part_pass_kernel<KW, RPT, MODE>;
+  const void* fn = (const void*)part_pass_kernel<KW, RPT, MODE, GROUP>;
   u64 grid = grid_for(fn, kPartThreads, 0, num_sms);
   if (grid > tiles) grid = tiles;
-  part_pass_kernel<KW, RPT, MODE><<<(unsigned)grid, kPartThreads, 0, stream>>>(g, r);
+  part_pass_kernel<KW, RPT, MODE, GROUP><<<(unsigned)grid, kPartThreads, 0, stream>>>(g, r);
   return cudaGetLastError();
 }
 
 template <int KW, int RPT>
 static cudaError_t launch_pass_mode(const PartGeom& g, const PartRecords& r, unsigned mode, cudaStream_t stream,
                                     int num_sms) {
-  if (mode == kModeBloom) return launch_pass_rt<KW, RPT, kModeBloom>(g, r, stream, num_sms);
-  if (mode == kModeCount) return launch_pass_rt<KW, RPT, kModeCount>(g, r, stream, num_sms);
-  return launch_pass_rt<KW, RPT, kModeRecount>(g, r, stream, num_sms);
+  // equal-key grouping (heavy hitters) is built for the 2-records-per-lane passes that count
+  const bool group = g.group && RPT == 2;
+  if (mode == kModeBloom)
+    return group ? launch_pass_rt<KW, RPT, kModeBloom, true>(g, r, stream, num_sms)
+                 : launch_pass_rt<KW, RPT, kModeBloom, false>(g, r, stream, num_sms);
+  if (mode == kModeCount)
+    return group ? launch_pass_rt<KW, RPT, kModeCount, true>(g, r, stream, num_sms)
+                 : launch_pass_rt<KW, RPT, kModeCount, false>(g, r, stream, num_sms);
+  return launch_pass_rt<KW, RPT, kModeRecount, false>(g, r, stream, num_sms);
 }
 
 cudaError_t launch_keyfilter_build(const PartGeom& g, cudaStream_t stream, int num_sms) {

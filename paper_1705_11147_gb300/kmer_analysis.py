@@ -49,13 +49,13 @@ def make_params(k: int, max_bases: int, min_depth: int = 2, min_ext_count: int =
                 windows_per_thread: int = 0, ctas_per_sm: int = 0,
                 warp_aggregate: bool = False, n_parts: int = 1, part: int = 0,
                 slot_prefetch: int = 0, fault_inject: int = 0,
-                partitions: int = 0) -> capi.kma_params:
+                partitions: int = 0, heavy_hitters: bool = False) -> capi.kma_params:
     return capi.kma_params(k, min_depth, min_ext_count, qual_threshold, qual_offset,
                            int(bool(use_bloom)), int(bool(canonical)), max_bases, max_reads,
                            expected_distinct, bloom_fpr, table_capacity, expected_keys,
                            load_factor, staging_bytes, block_threads, windows_per_thread,
                            ctas_per_sm, int(bool(warp_aggregate)), n_parts, part, slot_prefetch,
-                           fault_inject, partitions)
+                           fault_inject, partitions, int(bool(heavy_hitters)))
 
 
 def plan(params: capi.kma_params) -> capi.kma_plan:

@@ -62,7 +62,7 @@ def assert_same(got, want, what=""):
             raise AssertionError(f"{what}: field {f} differs at rows {bad}: {a[bad]} vs {b[bad]}")
 
 
-GPU_ONLY = ("use_bloom", "load_factor", "table_capacity", "block_threads", "windows_per_thread",
+GPU_ONLY = ("use_bloom", "heavy_hitters", "partitions", "load_factor", "table_capacity", "block_threads", "windows_per_thread",
             "warp_aggregate", "ctas_per_sm", "expected_distinct", "expected_keys", "staging_bytes",
             "max_bases", "max_reads", "bloom_fpr")
 
@@ -134,7 +134,9 @@ def test_low_complexity_and_repeats(gpu):
         # partitioned: the repeated k-mers overfill their buckets and spill into the
         # overflow area
         for bloom in (False, True):
-            assert_same(run_gpu(gpu, rs, partitions=5, use_bloom=bloom), want, f"k={k} partitioned")
+            for heavy in (False, True):
+                assert_same(run_gpu(gpu, rs, partitions=5, use_bloom=bloom, heavy_hitters=heavy), want,
+                            f"k={k} partitioned bloom={bloom} heavy_hitters={heavy}")
 
 
 def test_edge_inputs(gpu):
@@ -203,6 +205,8 @@ def test_results_independent_of_tuning(gpu, plain, shape):
     dict(partitions=4096),                      # many tiny partitions
     dict(partitions=5, use_bloom=False, min_depth=2),
     dict(partitions=3, expected_distinct=50_000, bloom_fpr=0.3, table_capacity=9_000_000),
+    dict(partitions=9, heavy_hitters=True),
+    dict(partitions=9, heavy_hitters=True, use_bloom=False, min_depth=2),
 ])
 def test_partitioned_mode(gpu, plain, opts):
     """On-chip owner-computes partitions give the same records as one table."""
@@ -558,3 +562,24 @@ def test_contigs_plain_and_bacterial(gpu, plain):
     _check_contigs(gpu, rs, rs.meta["params"]["k"])
     rb = synth.workload("bacterial_5m", scale=0.2)
     _check_contigs(gpu, rb, rb.meta["params"]["k"], partitions=4)
+
+
+def test_heavy_hitters_satellite(gpu):
+    """A tandem satellite making up a third of the reads (its k-mers occur tens of thousands
+    of times each): grouping equal keys in the warp (heavy_hitters) changes no record."""
+    rng = np.random.default_rng(21)
+    unit = "".join("ACGT"[i] for i in rng.integers(0, 4, 171))
+    g = "".join("ACGT"[i] for i in rng.integers(0, 4, 200_000))
+    sat = unit * 60
+    reads = []
+    for i in range(6000):
+        src = sat if i % 3 == 0 else g
+        a = int(rng.integers(0, len(src) - 150))
+        r = src[a:a + 150]
+        reads.append(r if i % 2 else r.translate(str.maketrans("ACGT", "TGCA"))[::-1])
+    rs = readset(reads, k=31, min_depth=2, min_ext_count=2, qual_threshold=20)
+    want = oracle_for(rs)
+    for bloom in (True, False):
+        for parts in (4, 1):
+            got = run_gpu(gpu, rs, partitions=parts, use_bloom=bloom, heavy_hitters=True)
+            assert_same(got, want, f"bloom={bloom} partitions={parts}")
