@@ -441,7 +441,8 @@ def run_ours(args, ws, rank, local):
 
 def run_e2e(args, ka, rs, dev, qkeys_dev, ws):
     """Same metric through the public API from pinned host buffers: host->device copies of the
-    reads, the whole path, and device->host copies of the records and query answers."""
+    reads, the whole path, and device->host copies of the records (finalize_to_host) and of the
+    query answers."""
     import torch
     seq_h = torch.from_numpy(rs.seq).pin_memory()
     qual_h = torch.from_numpy(rs.qual).pin_memory()
@@ -462,16 +463,28 @@ def run_e2e(args, ka, rs, dev, qkeys_dev, ws):
     seq_np, qual_np = seq_h.numpy(), qual_h.numpy()
     offs_np = offs_h.numpy().view(np.uint64)
 
+    phases = {}
+
     def step():
+        # host wall time of each call (count returns once its input copies are done;
+        # finalize_to_host waits for the counting work still in flight, then recounts,
+        # classifies and copies the records out, group by group)
+        t = [time.perf_counter()]
         ka.reset()
+        t.append(time.perf_counter())
         capi.check(lib.kmer_analysis_count(ka.handle, seq_np.ctypes.data, qual_np.ctypes.data,
                                            offs_np.ctypes.data, rs.n_reads, 0), "count")
-        r = ka.finalize()
-        capi.check(lib.kmer_analysis_copy_result(ka.handle, r_keys.data_ptr(), r_counts.data_ptr(),
-                                                 r_ext.data_ptr(), r_codes.data_ptr(), out_cap, 0),
-                   "copy_result")
+        t.append(time.perf_counter())
+        r = capi.kma_result()
+        capi.check(lib.kmer_analysis_finalize_to_host(ka.handle, r_keys.data_ptr(), r_counts.data_ptr(),
+                                                      r_ext.data_ptr(), r_codes.data_ptr(), out_cap,
+                                                      ctypes.byref(r)), "finalize_to_host")
+        t.append(time.perf_counter())
         capi.check(lib.kmer_analysis_query(ka.handle, qk_h.data_ptr(), qn, q_counts.data_ptr(),
                                            q_ext.data_ptr(), q_codes.data_ptr(), 0), "query")
+        t.append(time.perf_counter())
+        for name, a, b in zip(("reset", "count", "finalize_to_host", "query"), t, t[1:]):
+            phases[name] = round((b - a) * 1e3, 2)
         return r
 
     for _ in range(max(1, min(args.warmup, 2))):
@@ -490,7 +503,7 @@ def run_e2e(args, ka, rs, dev, qkeys_dev, ws):
     d2h = n * (16 + 4 + 32 + 2) + qn * (4 + 32 + 2)
     return {"value": round(int(info.valid_windows) * (ws if ws > 1 else 1) / dt / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps,
-            "ms_per_step": round(dt * 1e3, 2)}
+            "ms_per_step": round(dt * 1e3, 2), "last_step_phases_ms": phases}
 
 
 # ------------------------------------------------------------------ batched (many samples)

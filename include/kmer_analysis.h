@@ -174,6 +174,20 @@ int kmer_analysis_finalize(kma_handle* h, kma_result* out);
 int kmer_analysis_copy_result(kma_handle* h, uint64_t* keys, uint32_t* counts, uint32_t* ext,
                               uint8_t* codes, uint64_t capacity, int on_device);
 
+/* kmer_analysis_finalize followed by kmer_analysis_copy_result into HOST buffers, with the
+ * copies overlapped: the recount (Section 5.1's exact second pass) and the classification
+ * run in groups of on-chip partitions (of table slots with one table), and each group's
+ * records are copied to the host while the next group is recounted. The records, their
+ * order aside, are those of finalize. Buffers hold `capacity` records each (keys[c][2],
+ * counts[c], ext[c][8], codes[c][2] as in kma_result); any pointer may be NULL to skip that
+ * array; pinned host memory gives full copy bandwidth. The device result stays valid
+ * (kma_result in *out, copy_result and query work as after finalize). Synchronises.
+ * Errors: as kmer_analysis_finalize; KMA_EFULL also when out->n > capacity: the handle IS
+ * finalized, the first `capacity` records were copied and copy_result can fetch them all.
+ * On any other error the buffers' contents are unspecified. */
+int kmer_analysis_finalize_to_host(kma_handle* h, uint64_t* keys, uint32_t* counts, uint32_t* ext,
+                                   uint8_t* codes, uint64_t capacity, kma_result* out);
+
 /* Look up n k-mers given as keys[n][2] in either orientation (read-only phase, Section
  * 4.2 GRO). Answers are in the query's orientation: counts[i], ext[i][8] (left A C G T,
  * right A C G T) and codes[i][2]; k-mers below min_depth or absent give count 0, zero

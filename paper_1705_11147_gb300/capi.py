@@ -83,6 +83,7 @@ _SIGS = {
     "kmer_analysis_count": ([vp, vp, vp, vp, u64, ctypes.c_int], ctypes.c_int),
     "kmer_analysis_finalize": ([vp, ctypes.POINTER(kma_result)], ctypes.c_int),
     "kmer_analysis_copy_result": ([vp, vp, vp, vp, vp, u64, ctypes.c_int], ctypes.c_int),
+    "kmer_analysis_finalize_to_host": ([vp, vp, vp, vp, vp, u64, ctypes.POINTER(kma_result)], ctypes.c_int),
     "kmer_analysis_query": ([vp, vp, u64, vp, vp, vp, ctypes.c_int], ctypes.c_int),
     "kmer_analysis_reset": ([vp], ctypes.c_int),
     "kmer_analysis_set_stream": ([vp, vp], ctypes.c_int),

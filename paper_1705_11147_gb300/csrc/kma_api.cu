@@ -214,6 +214,11 @@ int get_pool(int dev, cudaMemPool_t* out) {
 
 }  // namespace
 
+// finalize_to_host splits the recount and classification into this many groups of
+// partitions (of table slots with one table), so that each group's records are copied to the
+// host while the next group is still being recounted.
+constexpr unsigned kFinalizeGroups = 8;
+
 struct kma_handle {
   kma_params p;
   Derived d;
@@ -268,6 +273,9 @@ struct kma_handle {
   unsigned char* out_codes = nullptr;
   u64 out_cap = 0;
   kma_result res;
+  // finalize_to_host: per-group record counts (pinned) and the events that publish them
+  u64* host_groups = nullptr;
+  cudaEvent_t group_ev[kFinalizeGroups] = {};
 
   // tracing
   bool profiling = false;
@@ -358,6 +366,12 @@ void free_all(kma_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->host_status) cudaFreeHost(h->host_status);
   h->host_status = nullptr;
+  if (h->host_groups) cudaFreeHost(h->host_groups);
+  h->host_groups = nullptr;
+  for (auto& e : h->group_ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   for (int i = 0; i < 2; ++i) {
     if (h->copied[i]) cudaEventDestroy(h->copied[i]);
     if (h->consumed[i]) cudaEventDestroy(h->consumed[i]);
@@ -517,9 +531,12 @@ int prepare_records(kma_handle* h, u64 n_pos, u64 n_reads, u64 n_bases, cudaStre
   return KMA_OK;
 }
 
-PartRecords records_of(const kma_handle::RecBatch& rb) {
+// Record batch `rb` of a handle with P partitions, all of it (every bucket, then the
+// overflow area).
+PartRecords records_of(const kma_handle::RecBatch& rb, u64 P) {
   PartRecords r;
   r.keys = rb.keys; r.info = rb.info; r.cap = rb.cap; r.ocap = rb.ocap; r.fill = rb.fill;
+  r.p_begin = 0; r.p_end = (unsigned)P; r.overflow = 1; r.pad = 0;
   return r;
 }
 
@@ -529,7 +546,7 @@ int scatter_windows(kma_handle* h, size_t index, u64 q0, u64 n_pos, cudaStream_t
   PartWindows w;
   w.codes = h->codes; w.rcodes = h->rcodes; w.inv = h->inv; w.hq = h->hq;
   w.q0 = q0; w.q1 = q0 + n_pos;
-  const PartRecords r = records_of(h->rec_batches[index]);
+  const PartRecords r = records_of(h->rec_batches[index], h->d.P);
   return timed_launch(h, KMA_KERNEL_SCATTER, st, n_pos > 0,
                       [&] { return launch_part_scatter(g, w, r, st, h->num_sms); });
 }
@@ -538,7 +555,7 @@ int scatter_windows(kma_handle* h, size_t index, u64 q0, u64 n_pos, cudaStream_t
 int record_pass(kma_handle* h, size_t index, cudaStream_t st) {
   const unsigned mode = h->p.use_bloom ? kModeBloom : kModeCount;
   const PartGeom g = part_geom(h);
-  const PartRecords r = records_of(h->rec_batches[index]);
+  const PartRecords r = records_of(h->rec_batches[index], h->d.P);
   return timed_launch(h, KMA_KERNEL_PASS, st, true, [&] { return launch_part_pass(g, r, mode, st, h->num_sms); });
 }
 
@@ -818,8 +835,7 @@ static int enqueue_recount(kma_handle* const* hs, uint32_t n) {
                       [&] { return launch_keyfilter_build(g, h0->stream, h0->num_sms); });
     if (rc) return rc;
     for (auto& rb : h->rec_batches) {
-      PartRecords r;
-      r.keys = rb.keys; r.info = rb.info; r.cap = rb.cap; r.ocap = rb.ocap; r.fill = rb.fill;
+      const PartRecords r = records_of(rb, h->d.P);
       rc = timed_launch(h0, KMA_KERNEL_RECOUNT, h0->stream, true,
                         [&] { return launch_part_pass(g, r, kModeRecount, h0->stream, h0->num_sms); });
       if (rc) return rc;
@@ -1030,6 +1046,112 @@ int kmer_analysis_copy_result(kma_handle* h, uint64_t* keys, uint32_t* counts, u
   }
   KMA_CUDA(cudaStreamSynchronize(h->stream));
   return KMA_OK;
+}
+
+int kmer_analysis_finalize_to_host(kma_handle* h, uint64_t* keys, uint32_t* counts, uint32_t* ext,
+                                   uint8_t* codes, uint64_t capacity, kma_result* out) {
+  if (!h) return KMA_EINVAL;
+  if (h->finalized || h->failed) return KMA_ESTATE;
+  if (!h->host_groups) {
+    KMA_CUDA(cudaMallocHost((void**)&h->host_groups, kFinalizeGroups * sizeof(u64)));
+    for (auto& e : h->group_ev) KMA_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  if (!h->copy_stream) KMA_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+  // Everything counted so far: the keys in the table bound the records.
+  int rc = read_status(h);
+  if (rc) return rc;
+  if ((rc = flags_to_code(h->host_status->flags))) { h->failed = true; return rc; }
+  if ((rc = ensure_output(h, h->host_status->table_keys))) { h->failed = true; return rc; }
+  KMA_CUDA(cudaMemsetAsync(&h->status->n_out, 0, 2 * sizeof(u64), h->stream));
+  const bool parts = h->d.P > 1;
+  const bool recount_parts = parts && h->p.use_bloom;
+  const u64 S = h->d.plan.table_slots;
+  const unsigned G = (unsigned)std::max<u64>(1, std::min<u64>(kFinalizeGroups, parts ? h->d.P : S / kClassTile));
+  const PartGeom g = part_geom(h);
+  // What the groups do not split: the one-table recount (a pass over the windows), or the
+  // overflow records of every partition.
+  if (h->p.use_bloom && !parts) {
+    kma_handle* hs[1] = {h};
+    if ((rc = enqueue_recount(hs, 1))) return rc;
+  }
+  if (recount_parts) {
+    if ((rc = timed_launch(h, KMA_KERNEL_RECOUNT, h->stream, g.Wk > 0,
+                           [&] { return launch_keyfilter_build(g, h->stream, h->num_sms); })))
+      return rc;
+    for (auto& rb : h->rec_batches) {
+      PartRecords r = records_of(rb, h->d.P);
+      r.p_end = 0;  // overflow area only
+      if ((rc = timed_launch(h, KMA_KERNEL_RECOUNT, h->stream, true,
+                             [&] { return launch_part_pass(g, r, kModeRecount, h->stream, h->num_sms); })))
+        return rc;
+    }
+  }
+  // Per group: recount its partitions, classify its slots (the records append to the output),
+  // publish the record count so far.
+  for (unsigned i = 0; i < G; ++i) {
+    u64 s0, s1;
+    if (parts) {
+      const u64 p0 = h->d.P * i / G, p1 = h->d.P * (i + 1) / G;
+      s0 = p0 * h->d.Sp;
+      s1 = p1 * h->d.Sp;
+      if (recount_parts) {
+        for (auto& rb : h->rec_batches) {
+          PartRecords r = records_of(rb, h->d.P);
+          r.p_begin = (unsigned)p0;
+          r.p_end = (unsigned)p1;
+          r.overflow = 0;
+          if ((rc = timed_launch(h, KMA_KERNEL_RECOUNT, h->stream, p1 > p0,
+                                 [&] { return launch_part_pass(g, r, kModeRecount, h->stream, h->num_sms); })))
+            return rc;
+        }
+      }
+    } else {
+      s0 = S * i / G;
+      s1 = S * (i + 1) / G;
+    }
+    ClassBatch cb;
+    std::memset(&cb, 0, sizeof(cb));
+    cb.write = 1;
+    cb.n = 1;
+    cb.d[0] = class_desc(h);
+    cb.d[0].table = h->table + s0;
+    cb.d[0].slots = s1 - s0;
+    cb.total_blocks = (s1 - s0 + kClassTile - 1) / kClassTile;
+    if ((rc = timed_launch(h, KMA_KERNEL_CLASSIFY, h->stream, cb.total_blocks > 0,
+                           [&] { return launch_classify(cb, h->stream, h->num_sms); })))
+      return rc;
+    KMA_CUDA(cudaMemcpyAsync(&h->host_groups[i], &h->status->n_out, sizeof(u64), cudaMemcpyDeviceToHost, h->stream));
+    KMA_CUDA(cudaEventRecord(h->group_ev[i], h->stream));
+  }
+  KMA_CUDA(cudaMemcpyAsync(h->host_status, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+  // As each group completes, its records go to the host on the copy stream while the GPU
+  // recounts the next group.
+  const u64 cap = std::min<u64>(capacity, h->out_cap);
+  u64 done = 0;
+  for (unsigned i = 0; i < G; ++i) {
+    KMA_CUDA(cudaEventSynchronize(h->group_ev[i]));
+    const u64 upto = std::min<u64>(h->host_groups[i], cap);
+    if (upto <= done) continue;
+    const u64 n = upto - done;
+    KMA_CUDA(cudaStreamWaitEvent(h->copy_stream, h->group_ev[i], 0));
+    if (keys) KMA_CUDA(cudaMemcpyAsync(keys + 2 * done, h->out_keys + 2 * done, n * 16, cudaMemcpyDeviceToHost, h->copy_stream));
+    if (counts) KMA_CUDA(cudaMemcpyAsync(counts + done, h->out_counts + done, n * 4, cudaMemcpyDeviceToHost, h->copy_stream));
+    if (ext) KMA_CUDA(cudaMemcpyAsync(ext + 8 * done, h->out_ext + 8 * done, n * 32, cudaMemcpyDeviceToHost, h->copy_stream));
+    if (codes) KMA_CUDA(cudaMemcpyAsync(codes + 2 * done, h->out_codes + 2 * done, n * 2, cudaMemcpyDeviceToHost, h->copy_stream));
+    done = upto;
+  }
+  free_records(h);
+  KMA_CUDA(cudaStreamSynchronize(h->stream));
+  KMA_CUDA(cudaStreamSynchronize(h->copy_stream));
+  if ((rc = flags_to_code(h->host_status->flags))) {
+    h->failed = true;
+    if (out) std::memset(out, 0, sizeof(kma_result));
+    return rc;
+  }
+  fill_result(h);
+  h->finalized = true;
+  if (out) *out = h->res;
+  return h->res.n > capacity ? KMA_EFULL : KMA_OK;
 }
 
 int kmer_analysis_query(kma_handle* h, const uint64_t* keys, uint64_t n, uint32_t* counts,

@@ -196,6 +196,10 @@ struct PartRecords {
   unsigned long long cap;       // records per bucket
   unsigned long long ocap;      // overflow records
   unsigned long long* fill;     // [P + 1]
+  // record passes: the buckets of partitions [p_begin, p_end), then the overflow area if
+  // `overflow` (the whole batch: 0, P, 1); the scatter ignores these
+  unsigned int p_begin, p_end;
+  unsigned int overflow, pad;
 };
 
 cudaError_t launch_part_scatter(const PartGeom& g, const PartWindows& w, const PartRecords& r,

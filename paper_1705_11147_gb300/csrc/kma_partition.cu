@@ -211,19 +211,22 @@ static_assert(sizeof(WarpStage<1, 2>) % 16 == 0 && sizeof(WarpStage<2, 2>) % 16 
                   sizeof(WarpStage<1, 4>) % 16 == 0 && sizeof(WarpStage<2, 4>) % 16 == 0,
               "every warp's staging buffers must start on a 16-byte boundary");
 
-// Record range [base, end) of tile t, clipped to one tile; false if the tile is empty.
+// Record range [base, end) of tile t, clipped to one tile; false if the tile is empty. The
+// launch numbers its tiles from 0: first the nb tiles of the buckets of partitions
+// [p_begin, p_end), then the tiles of the overflow area (if the launch covers it).
 template <int TILE>
-__device__ __forceinline__ bool rec_tile(const PartGeom& G, const PartRecords& R, u64 tpb, u64 t, u64& base,
-                                         u64& end) {
+__device__ __forceinline__ bool rec_tile(const PartGeom& G, const PartRecords& R, u64 tpb, u64 nb, u64 t,
+                                         u64& base, u64& end) {
   u64 f, lo, b0;
-  if (t < (u64)G.P * tpb) {
+  if (t < nb) {
+    t += (u64)R.p_begin * tpb;
     const u64 b = ((t | tpb) >> 32) ? t / tpb : (u64)((unsigned)t / (unsigned)tpb);
     f = R.fill[b] < R.cap ? R.fill[b] : R.cap;
     lo = (t - b * tpb) * TILE;
     b0 = b * R.cap;
   } else {
     f = R.fill[G.P] < R.ocap ? R.fill[G.P] : R.ocap;
-    lo = (t - (u64)G.P * tpb) * TILE;
+    lo = (t - nb) * TILE;
     b0 = (u64)G.P * R.cap;
   }
   if (lo >= f) return false;
@@ -234,10 +237,10 @@ __device__ __forceinline__ bool rec_tile(const PartGeom& G, const PartRecords& R
 
 // First non-empty tile at or after t in steps of `step` (n_tiles if none).
 template <int TILE>
-__device__ __forceinline__ u64 rec_next(const PartGeom& G, const PartRecords& R, u64 tpb, u64 n_tiles, u64 t,
-                                        u64 step, u64& base, u64& end) {
+__device__ __forceinline__ u64 rec_next(const PartGeom& G, const PartRecords& R, u64 tpb, u64 nb, u64 n_tiles,
+                                        u64 t, u64 step, u64& base, u64& end) {
   base = end = 0;
-  while (t < n_tiles && !rec_tile<TILE>(G, R, tpb, t, base, end)) t += step;
+  while (t < n_tiles && !rec_tile<TILE>(G, R, tpb, nb, t, base, end)) t += step;
   return t;
 }
 
@@ -268,7 +271,8 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
   const u64 step = (u64)gridDim.x * kWarps;
   const u64 tpb = (R.cap + kTile - 1) / kTile;  // tiles per bucket
   const u64 ofill = R.fill[G.P] < R.ocap ? R.fill[G.P] : R.ocap;
-  const u64 n_tiles = (u64)G.P * tpb + (ofill + kTile - 1) / kTile;
+  const u64 nb = (u64)(R.p_end - R.p_begin) * tpb;  // bucket tiles of this launch
+  const u64 n_tiles = nb + (R.overflow ? (ofill + kTile - 1) / kTile : 0);
   const u64 pol = policy_evict_first();
   u64 acc_ins = 0, acc_first = 0;
   unsigned phases = 0;  // bit b: parity to wait for on buffer b (same in every lane)
@@ -277,7 +281,7 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
   if (lane == 0) {
     mbar_init(smem_u32(&S.bar[0]), 1);
     mbar_init(smem_u32(&S.bar[1]), 1);
-    t = rec_next<kTile>(G, R, tpb, n_tiles, (u64)blockIdx.x * kWarps + warp, step, base, end);
+    t = rec_next<kTile>(G, R, tpb, nb, n_tiles, (u64)blockIdx.x * kWarps + warp, step, base, end);
     if (t < n_tiles) rec_issue(S, R, 0, base, end, pol);
   }
   __syncwarp();  // barriers initialised before any lane polls them
@@ -287,13 +291,13 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
   int buf = 0;
   while (t < n_tiles) {
     // prefetch the warp's next non-empty tile into the other buffer, then wait for this one
-    u64 tn, nb, ne;
+    u64 tn, nbase, ne;
     if (lane == 0) {
-      tn = rec_next<kTile>(G, R, tpb, n_tiles, t + step, step, nb, ne);
-      if (tn < n_tiles) rec_issue(S, R, buf ^ 1, nb, ne, pol);
+      tn = rec_next<kTile>(G, R, tpb, nb, n_tiles, t + step, step, nbase, ne);
+      if (tn < n_tiles) rec_issue(S, R, buf ^ 1, nbase, ne, pol);
     }
     tn = shfl0(tn);
-    nb = shfl0(nb);
+    nbase = shfl0(nbase);
     ne = shfl0(ne);
     const unsigned bar = smem_u32(&S.bar[buf]);
     const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, (phases >> buf) & 1u, G.wait_limit));
@@ -476,7 +480,7 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
     }
     __syncwarp();  // buffer `buf` (and the list) are free for the next copy
     t = tn;
-    base = nb;
+    base = nbase;
     end = ne;
     buf ^= 1;
   }
@@ -544,7 +548,9 @@ cudaError_t launch_part_scatter(const PartGeom& g, const PartWindows& w, const P
 template <int KW, int RPT, unsigned MODE, bool GROUP>
 static cudaError_t launch_pass_rt(const PartGeom& g, const PartRecords& r, cudaStream_t stream, int num_sms) {
   constexpr int tile = 32 * RPT;
-  const u64 tiles = (u64)g.P * ((r.cap + tile - 1) / tile) + (r.ocap + tile - 1) / tile;
+  if (r.p_begin > r.p_end || r.p_end > g.P) return cudaErrorInvalidValue;
+  const u64 tiles = (u64)(r.p_end - r.p_begin) * ((r.cap + tile - 1) / tile) +
+                    (r.overflow ? (r.ocap + tile - 1) / tile : 0);
   if (tiles == 0) return cudaSuccess;
   if ((r.cap | r.ocap) & 15 || (reinterpret_cast<uintptr_t>(r.keys) | reinterpret_cast<uintptr_t>(r.info)) & 15)
     return cudaErrorInvalidValue;  // staging needs 16-record buckets on 16-byte boundaries

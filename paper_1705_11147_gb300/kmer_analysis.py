@@ -137,6 +137,27 @@ class KmerAnalysis:
               "copy_result")
         return Result(keys, counts, ext, codes, int(r.n_uu), int(r.valid_windows), int(r.table_keys))
 
+    def finalize_to_host(self, out):
+        """finalize + copy of the records to host arrays in one call, the copies of one group
+        of partitions overlapping the recount of the next (kmer_analysis_finalize_to_host).
+        `out` = (keys[c, 2] u64, counts[c] u32, ext[c, 8] u32, codes[c, 2] u8) host arrays of
+        c rows (host_result_buffers; pinned memory copies fastest). Returns a Result viewing
+        the first n rows; raises KmaError (KMA_EFULL) if n > c, the handle then finalized."""
+        keys, counts, ext, codes = (np.asarray(a) for a in out)
+        assert keys.dtype == np.uint64 and counts.dtype == np.uint32 and ext.dtype == np.uint32
+        assert codes.dtype == np.uint8 and all(a.flags.c_contiguous for a in (keys, counts, ext, codes))
+        cap = min(keys.shape[0], counts.shape[0], ext.shape[0], codes.shape[0])
+        r = capi.kma_result()
+        rc = self._lib.kmer_analysis_finalize_to_host(self._h, keys.ctypes.data, counts.ctypes.data,
+                                                      ext.ctypes.data, codes.ctypes.data, cap,
+                                                      ctypes.byref(r))
+        if rc == 0 or (rc == capi.KMA_EFULL and int(r.n) > cap):
+            self.result_info = r
+        check(rc, "finalize_to_host")
+        n = int(r.n)
+        return Result(keys[:n], counts[:n], ext[:n], codes[:n], int(r.n_uu), int(r.valid_windows),
+                      int(r.table_keys))
+
     def contigs(self):
         """Contigs of the finalized result (kmer_analysis_contigs, Section 5.2): (list of
         strings, info) with info = {n_contigs, n_bases, n_vertices, n_cycles}."""
@@ -231,6 +252,18 @@ class KmerAnalysis:
 
     def __exit__(self, *exc):
         self.destroy()
+
+
+def host_result_buffers(capacity: int, pinned: bool = False):
+    """Host arrays for `capacity` records in the layout of kma_result (keys, counts, ext,
+    codes), optionally in pinned (page-locked) memory."""
+    shapes = (((capacity, 2), np.uint64), ((capacity,), np.uint32), ((capacity, 8), np.uint32),
+              ((capacity, 2), np.uint8))
+    if not pinned:
+        return tuple(np.zeros(sh, dt) for sh, dt in shapes)
+    torch = _torch()
+    tdt = {np.uint64: torch.int64, np.uint32: torch.int32, np.uint8: torch.uint8}
+    return tuple(torch.empty(sh, dtype=tdt[dt]).pin_memory().numpy().view(dt) for sh, dt in shapes)
 
 
 def count_batch(handles: list[KmerAnalysis], reads: list[tuple]) -> None:

@@ -583,3 +583,79 @@ def test_heavy_hitters_satellite(gpu):
         for parts in (4, 1):
             got = run_gpu(gpu, rs, partitions=parts, use_bloom=bloom, heavy_hitters=True)
             assert_same(got, want, f"bloom={bloom} partitions={parts}")
+
+
+# ------------------------------------------------------------------ finalize straight to host
+
+def run_gpu_to_host(torch, rs, capacity=None, pinned=True, **kw):
+    """count (device inputs) + kmer_analysis_finalize_to_host into host buffers; returns the
+    sorted records and the handle's own finalize result for cross-checks."""
+    from paper_1705_11147_gb300 import KmerAnalysis, host_result_buffers, make_params
+    p = dict(rs.meta.get("params", {}))
+    p.pop("bloom_fpr", None)
+    p.update(kw)
+    p.setdefault("max_bases", max(rs.n_bases, 1))
+    p.setdefault("max_reads", max(rs.n_reads, 1))
+    p.setdefault("expected_distinct", max(rs.n_bases, 1))
+    cap = rs.n_bases + 1 if capacity is None else capacity
+    with KmerAnalysis(make_params(**p)) as ka:
+        ka.count(*to_dev(torch, rs))
+        got = ka.finalize_to_host(host_result_buffers(cap, pinned=pinned))
+        again = ka.copy_result()  # the device result stays valid
+        return got.sorted(), again.sorted()
+
+
+@pytest.mark.parametrize("opts", [
+    dict(),
+    dict(use_bloom=False, min_depth=1),
+    dict(partitions=7),
+    dict(partitions=64),
+    dict(partitions=4096),
+    dict(partitions=5, use_bloom=False, min_depth=2),
+    dict(partitions=9, heavy_hitters=True),
+])
+def test_finalize_to_host(gpu, plain, opts):
+    """The grouped recount + classification with overlapped copies gives finalize's records."""
+    rs, want = plain
+    got, again = run_gpu_to_host(gpu, rs, **opts)
+    assert_same(again, got, f"copy_result after finalize_to_host {opts}")
+    if opts.get("min_depth", 2) == 2:
+        assert_same(got, want, str(opts))
+    else:
+        rs2 = synth.ReadSet(rs.seq, rs.qual, rs.offsets)
+        rs2.meta["params"] = dict(rs.meta["params"], min_depth=opts["min_depth"])
+        assert_same(got, oracle_for(rs2), str(opts))
+
+
+def test_finalize_to_host_overflow_capacity_and_query(gpu):
+    """Repeated k-mers spill into the overflow area (recounted before the groups); too small a
+    host buffer gets the first `capacity` records and KMA_EFULL, with the handle finalized."""
+    from paper_1705_11147_gb300 import KMA_EFULL, KmaError, KmerAnalysis, host_result_buffers, make_params
+    reads = ["A" * 300, "AC" * 150, "ACGT" * 75, "GATTACA" * 40, "T" * 70 + "G" + "T" * 70] * 40
+    rr = synth.random_reads(seed=99, n_reads=3000, min_len=60, max_len=200, alphabet=b"ACGT", q_lo=15, q_hi=40)
+    strs = reads + [bytes(rr.seq[rr.offsets[i]:rr.offsets[i + 1]]).decode() for i in range(rr.n_reads)] * 2
+    rs = readset(strs, k=31, min_depth=2, min_ext_count=2, qual_threshold=20)
+    want = oracle_for(rs)
+    for parts in (5, 1):
+        got, _ = run_gpu_to_host(gpu, rs, partitions=parts, pinned=False)
+        assert_same(got, want, f"partitions={parts}")
+    n = len(want)
+    p = dict(k=31, min_depth=2, min_ext_count=2, qual_threshold=20, max_bases=rs.n_bases, max_reads=rs.n_reads,
+             expected_distinct=rs.n_bases, partitions=5)
+    with KmerAnalysis(make_params(**p)) as ka:
+        ka.count(*to_dev(gpu, rs))
+        bufs = host_result_buffers(n // 3)
+        with pytest.raises(KmaError) as ei:
+            ka.finalize_to_host(bufs)
+        assert ei.value.code == KMA_EFULL
+        assert int(ka.result_info.n) == n
+        keys = bufs[0]
+        idx = {tuple(k): i for i, k in enumerate(want.keys.tolist())}
+        for j in range(n // 3):  # every copied row is a correct record
+            i = idx[tuple(keys[j].tolist())]
+            assert bufs[1][j] == want.counts[i] and np.array_equal(bufs[2][j], want.ext[i])
+            assert np.array_equal(bufs[3][j], want.codes[i])
+        assert len({tuple(k) for k in keys.tolist()}) == n // 3
+        assert_same(ka.copy_result().sorted(), want, "copy_result after a short buffer")
+        counts, ext, codes = ka.query(want.keys[:100])
+        assert np.array_equal(counts, want.counts[:100])
