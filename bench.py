@@ -583,7 +583,7 @@ def run_batched(args, ws, rank, local):
             "plain": {"value": round(plain_value, 3), "unit": UNIT, "ms_per_step": round(ms_plain, 2),
                       "path": "create -> count -> finalize -> destroy per sample"},
             "batched_vs_plain": round(value / plain_value, 3), "gpu_launches": int(launches),
-            "clocks": clk, "generation_s": round(t_gen, 1), "sizing_pass": sizing, "contigs": contigs}
+            "clocks": clk, "generation_s": round(t_gen, 1)}
 
 
 # ------------------------------------------------------------------ served (job stream)
