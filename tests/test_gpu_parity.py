@@ -659,3 +659,52 @@ def test_finalize_to_host_overflow_capacity_and_query(gpu):
         assert_same(ka.copy_result().sorted(), want, "copy_result after a short buffer")
         counts, ext, codes = ka.query(want.keys[:100])
         assert np.array_equal(counts, want.counts[:100])
+
+
+# ------------------------------------------------------------------ every batched sample, served subset
+
+@pytest.mark.slow
+def test_batched_64_every_sample_vs_oracle(gpu):
+    """All 64 samples of the batched workload (genome sizes scaled to 0.5 %, the rest of the
+    recipe unchanged) through one captured graph, the bench's batched path: every sample's
+    records equal the oracle's."""
+    from paper_1705_11147_gb300 import BatchGraph, KmerAnalysis, make_params
+    sets = [synth.sample_reads(s) for s in synth.batched_specs(64, scale=0.005)]
+    handles = [KmerAnalysis(make_params(k=51, min_depth=2, qual_threshold=20, max_bases=rs.n_bases,
+                                        max_reads=rs.n_reads, expected_distinct=rs.n_bases,
+                                        partitions=1 if i % 4 else 3))
+               for i, rs in enumerate(sets)]
+    g = BatchGraph(handles, [to_dev(gpu, rs) for rs in sets])
+    g.replay()
+    g.results()
+    for i, (h, rs) in enumerate(zip(handles, sets)):
+        assert_same(h.copy_result().sorted(), oracle.run_readset(rs), f"sample {i}")
+        h.destroy()
+
+
+@pytest.mark.slow
+def test_served_subset_vs_oracle(gpu):
+    """30 jobs of the served workload (genomes scaled to 0.2 %), the smallest and the largest
+    of all 500 among them, through the batching server: every job equals the oracle."""
+    from paper_1705_11147_gb300.serve import Job, Server
+    specs = synth.served_specs(500, scale=0.002)
+    by_size = sorted(range(len(specs)), key=lambda j: specs[j]["G"])
+    pick = {by_size[0], by_size[-1]}
+    j = 0
+    while len(pick) < 30:
+        pick.add(j)
+        j += 1
+    pick = sorted(pick)
+    jobs, sets = [], []
+    for i in pick:
+        rs = synth.sample_reads(specs[i])
+        p = dict(rs.meta["params"])
+        p.pop("bloom_fpr")
+        p["expected_distinct"] = rs.n_bases
+        jobs.append(Job(rs.seq, rs.qual, rs.offsets, params=p, job_id=i))
+        sets.append(rs)
+    assert len(jobs) == 30 and {j.params["k"] for j in jobs} == {31, 51}
+    with Server(max_batch=8, workers=2) as srv:
+        got = [f.result(timeout=600) for f in [srv.submit(j) for j in jobs]]
+    for i, (res, rs) in enumerate(zip(got, sets)):
+        assert_same(res.sorted(), oracle.run_readset(rs), f"job {pick[i]}")
