@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/kmer_analysis.h"
@@ -703,6 +704,25 @@ int kmer_analysis_create(const kma_params* params, void* cuda_stream, kma_handle
   return KMA_OK;
 }
 
+// offsets[0..n] non-decreasing? Large read sets are checked by several host threads (the
+// check is a stream over 8 bytes per read, done before any input is copied).
+static bool offsets_nondecreasing(const uint64_t* offsets, u64 n) {
+  auto check = [offsets](u64 a, u64 b) {
+    unsigned bad = 0;
+    for (u64 r = a; r < b; ++r) bad |= offsets[r + 1] < offsets[r];
+    return bad == 0;
+  };
+  const unsigned hw = std::thread::hardware_concurrency();
+  const unsigned T = n < (1u << 20) ? 1u : std::max(1u, std::min(8u, hw));
+  if (T == 1) return check(0, n);
+  std::vector<char> ok(T, 0);
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < T; ++t)
+    th.emplace_back([&, t] { ok[t] = check(n * t / T, n * (t + 1) / T); });
+  for (auto& x : th) x.join();
+  return std::all_of(ok.begin(), ok.end(), [](char v) { return v != 0; });
+}
+
 static int setup_staging(kma_handle* h) {
   if (h->stage_seq[0]) return KMA_OK;
   int rc;
@@ -745,8 +765,7 @@ int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual, const 
   }
   // Host input: validate offsets, then stream chunks through two staging buffers; the copy
   // of chunk i+1 overlaps the packing and first pass of chunk i.
-  for (u64 r = 0; r < n_reads; ++r)
-    if (offsets[r + 1] < offsets[r]) return KMA_EINVAL;
+  if (!offsets_nondecreasing(offsets, n_reads)) return KMA_EINVAL;
   if (offsets[n_reads] - offsets[0] + h->bases_used > h->p.max_bases) return KMA_EFULL;
   if ((rc = setup_staging(h))) return rc;
   // With partitions, every staged chunk is packed and scattered into one set of record buckets

@@ -153,6 +153,25 @@ def test_edge_inputs(gpu):
     assert got.counts.tolist() == [2]
 
 
+def test_decreasing_host_offsets_rejected(gpu):
+    """Host read offsets that decrease anywhere (checked by one thread, or by several for a
+    million reads and more) are rejected before anything is copied; the handle stays usable."""
+    from paper_1705_11147_gb300 import KMA_EINVAL, KmaError, KmerAnalysis, make_params
+    good = readset(["ACGTTGCAAGGCTTAGCCATG" * 3] * 4, k=21, min_depth=1, min_ext_count=1, qual_threshold=20)
+    with KmerAnalysis(make_params(k=21, min_depth=1, use_bloom=False, max_bases=4096, max_reads=64)) as ka:
+        seq = np.full(64, ord("A"), np.uint8)
+        for n in (3, (1 << 20) + 5):
+            for at in (0, n // 2, n - 1):
+                offs = np.full(n + 1, 8, np.uint64)
+                offs[: at + 1] = 9                   # offsets[at] = 9 > offsets[at + 1] = 8
+                with pytest.raises(KmaError) as e:
+                    ka.count(seq, seq, offs)
+                assert e.value.code == KMA_EINVAL, (n, at)
+        ka.count(good.seq, good.qual, good.offsets)
+        ka.finalize()
+        assert_same(ka.copy_result().sorted(), oracle_for(good, use_bloom=False), "after rejected calls")
+
+
 # ------------------------------------------------------------------ workloads
 
 @pytest.fixture(scope="module")
