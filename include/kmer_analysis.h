@@ -144,8 +144,11 @@ typedef struct {
 int kmer_analysis_plan(const kma_params* params, kma_plan* out);
 
 /* Allocate a handle: packed-read arena, Bloom filter, hash table, status words, staging.
- * `cuda_stream` is a cudaStream_t (NULL = default stream). The handle starts empty.
- * Errors: KMA_EINVAL (params), KMA_ENOMEM, KMA_ECUDA. On error *out is NULL. */
+ * `cuda_stream` is a cudaStream_t (NULL = default stream). The handle starts empty and belongs
+ * to the CUDA device that is current here; every later call on it must be made with that
+ * device current (the library does not switch devices). A handle is not thread-safe: one
+ * host thread at a time. Errors: KMA_EINVAL (params), KMA_ENOMEM, KMA_ECUDA. On error *out
+ * is NULL. */
 int kmer_analysis_create(const kma_params* params, void* cuda_stream, kma_handle** out);
 
 /* Add reads (Section 5.1 counting phase; may be called repeatedly with further batches).

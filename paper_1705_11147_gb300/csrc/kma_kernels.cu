@@ -199,15 +199,49 @@ __device__ __forceinline__ u64 base_at_or_after(const PackDesc& D, u64 o0, u64 r
   return b < D.n_bases ? b : D.n_bases;
 }
 
-// Bit i of x moved to bit 2i of the result (the other bits zero).
-__device__ __forceinline__ u64 spread_bits(unsigned x) {
-  u64 v = x;
-  v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
-  v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
-  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
-  v = (v | (v << 2)) & 0x3333333333333333ull;
-  v = (v | (v << 1)) & 0x5555555555555555ull;
-  return v;
+// Four bytes starting at byte offset a of a shared-memory buffer (read as two aligned words;
+// the buffer has slack past its last staged byte).
+__device__ __forceinline__ unsigned load4(const unsigned* w, unsigned a) {
+  const u64 v = ((u64)w[(a >> 2) + 1] << 32) | w[a >> 2];
+  return (unsigned)(v >> ((a & 3u) * 8u));
+}
+
+// First position of read rr + 1 relative to the chunk start P0 (saturated: past the last read
+// or beyond 32 bits).
+__device__ __forceinline__ unsigned pack_next_start(const u64* off, u64 o0, u64 P0, u64 nr, u64 rr) {
+  if (rr >= nr) return 0xFFFFFFFFu;
+  const u64 sn = off[rr + 1] - o0 + rr + 1 - P0;
+  return sn < 0xFFFFFFFFull ? (unsigned)sn : 0xFFFFFFFFu;
+}
+
+// Four positions that are all bases of one read: s = their sequence bytes, q = their quality
+// bytes (first position in the low byte). Byte-parallel arithmetic gives per byte the 2-bit
+// code (A0 C1 G2 T3 from bits 1..3 of the character, either case), whether the character is
+// A/C/G/T at all (it must equal the upper-case letter its code names), and code/valid/quality
+// flags; multiplications by sparse constants then gather the four results into
+//   f8: the four codes, first position in the top bits (forward words are MSB-first),
+//   r8: the four complemented codes, first position in the low bits (reverse words),
+//   i4: invalid flags and h4: high-quality flags, first position in bit 3.
+// An invalid position has code 0 and complemented code 3. gmask = 0 when no byte can reach
+// the quality threshold (threshold above 255).
+__device__ __forceinline__ void pack_group4(unsigned s, unsigned q, unsigned qmin4, unsigned gmask, unsigned& f8,
+                                            unsigned& r8, unsigned& i4, unsigned& h4) {
+  const unsigned H = 0x80808080u, L1 = 0x01010101u;
+  unsigned code = ((s >> 1) ^ (s >> 2)) & 0x03030303u;
+  const unsigned b0 = code & L1, b1 = (code >> 1) & L1;
+  const unsigned letter = 0x41414141u + 2u * b0 + 6u * b1 + 11u * (b0 & b1);  // A C G T
+  const unsigned d = (s & 0xDFDFDFDFu) ^ letter;
+  const unsigned nz = (((d & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | d) & H;  // bit 7: byte of d non-zero
+  const unsigned valid = (~nz & H) >> 7;
+  code &= valid * 3u;
+  // per byte q >= qmin (unsigned): the low 7 bits compared by a borrow-free subtraction
+  const unsigned sq = (q | H) - (qmin4 & ~H);
+  const unsigned ge = ((q & ~qmin4) | (~(q ^ qmin4) & sq)) & H;
+  const unsigned good = (ge >> 7) & valid & gmask;
+  f8 = (code * 0x40100401u) >> 24;                   // byte k's code to bits 6 - 2k
+  r8 = ((~code & 0x03030303u) * 0x01041040u) >> 24;  // byte k's complement to bits 2k
+  i4 = (((valid ^ L1) * 0x08040201u) >> 24) & 0xFu;  // byte k's flag to bit 3 - k
+  h4 = ((good * 0x08040201u) >> 24) & 0xFu;
 }
 
 constexpr int kPackThreads = 256;                     // 8 warps, one 64-position word per thread
@@ -216,19 +250,17 @@ constexpr int kPackBuf = kPackChunk + 32;             // staged bytes (+ alignme
 
 // One CTA chunk = 256 words of 64 arena positions of one sample. The bases (and qualities)
 // the chunk covers are one contiguous byte range of the input; thread 0 locates it and
-// stages it into shared memory with two 1-D TMA bulk copies. Each warp then packs 32 words,
-// 32 consecutive positions at a time (lane l takes position l, so shared-memory reads are
-// consecutive bytes): four warp votes give the two code bits, the invalid bit and the
-// high-quality bit of the 32 positions. At the end lane j turns the votes of word j into its
-// code, complemented-code, invalid and high-quality words (bit interleaving), so the words
-// are stored coalesced.
-__global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constant__ PackBatch B) {
+// stages it into shared memory with two 1-D TMA bulk copies. Thread t then builds word t of
+// the chunk (its code, complemented-code, invalid and high-quality words) four positions at
+// a time: four positions inside one read take the byte-parallel path (pack_group4), a group
+// that holds a read's separator or starts a new read is done position by position. The
+// words of consecutive threads are consecutive, so the stores coalesce.
+__global__ void __launch_bounds__(kPackThreads, 4) pack_kernel(const __grid_constant__ PackBatch B) {
   __shared__ __align__(16) unsigned char s_seq[kPackBuf];
   __shared__ __align__(16) unsigned char s_qual[kPackBuf];
   __shared__ __align__(8) unsigned long long s_bar;
   __shared__ u64 s_b0, s_b1, s_r0, s_r1;
   __shared__ unsigned s_lead, s_ok;
-  __shared__ uint4 s_bal[kPackThreads / 32][64];  // per warp: votes of its 64 32-position steps
   const unsigned bar = smem_u32(&s_bar);
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
@@ -308,58 +340,73 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
     if (s_ok == 2) return;  // uniform: the chunk's input never arrived
     const unsigned nb = (unsigned)(s_b1 - s_b0);  // staged bases
     const unsigned lead = s_lead & 0xFF, leadq = s_lead >> 8;
-    const unsigned lane = threadIdx.x & 31;
     const u64 ww0 = w0 + warp * 32;                  // first word of this warp
-    const u64 gw = (D.q0 >> 6) + w0 + threadIdx.x;  // the word this lane stores
+    const u64 gw = (D.q0 >> 6) + w0 + threadIdx.x;  // the word this thread stores
     if (ww0 < w1 && s_ok) {
       // Positions are handled relative to the chunk start P0 (32-bit). A base of read r at
       // position p has batch base index p - r; the chunk's staged bytes start at the base of
       // the chunk's first position, so its byte offset is (p - P0) - (r - r0).
       const u64 nr = D.n_reads, P0 = w0 * 64, r0 = s_r0;
-      u64 r = nr ? read_at_warp(off, o0, s_r0, s_r1 + 1, ww0 * 64) : 0;
-      // first position of read r + 1, relative to P0 (saturated: beyond the chunk)
-      auto next_start = [&](u64 rr) -> unsigned {
-        if (rr >= nr) return 0xFFFFFFFFu;
-        const u64 sn = off[rr + 1] - o0 + rr + 1 - P0;
-        return sn < 0xFFFFFFFFull ? (unsigned)sn : 0xFFFFFFFFu;
-      };
-      unsigned snext = next_start(r);
-      unsigned rd = (unsigned)(r - r0);  // read index relative to the chunk's first read
-      const unsigned nrd = (unsigned)(nr - r0);
-      uint4* bal = s_bal[warp];
-#pragma unroll 4
-      for (unsigned it = 0; it < 64; ++it) {
-        const unsigned pr = warp * 2048u + it * 32u + lane;
-        while (rd < nrd && pr >= snext) {  // the lane's read (reads may be shorter than 32)
-          ++rd;
-          snext = next_start(r0 + rd);
+      const u64 rw = nr ? read_at_warp(off, o0, s_r0, s_r1 + 1, ww0 * 64) : 0;
+      if (w0 + threadIdx.x < w1) {
+        // the read holding this word's first position (binary search from the warp's read)
+        const u64 pos = (w0 + threadIdx.x) * 64;
+        u64 lo = rw, hi = nr ? s_r1 + 1 : rw;
+        while (hi - lo > 1) {
+          const u64 mid = (lo + hi) >> 1;
+          if (off[mid] - o0 + mid <= pos) lo = mid; else hi = mid;
         }
-        unsigned code = 0, valid = 0, good = 0;
-        const unsigned bi = pr - rd;  // staged byte of this position, if it is a base
-        if (rd < nrd && pr + 1u != snext && bi < nb) {
-          const unsigned ch = s_seq[lead + bi];
-          const unsigned u = (ch & 0xDFu) - 0x40u;  // A C G T (either case) -> bits 1 3 7 20
-          valid = u < 32u ? (0x10008Au >> u) & 1u : 0u;
-          code = valid ? ((ch >> 1) ^ (ch >> 2)) & 3u : 0u;  // A0 C1 G2 T3
-          good = valid && (unsigned)s_qual[leadq + bi] >= D.qual_min;
+        unsigned rd = (unsigned)(lo - r0);  // read index relative to the chunk's first read
+        unsigned snext = pack_next_start(off, o0, P0, nr, lo);
+        const unsigned nrd = (unsigned)(nr - r0);
+        const unsigned* sw = reinterpret_cast<const unsigned*>(s_seq);
+        const unsigned* qw = reinterpret_cast<const unsigned*>(s_qual);
+        const unsigned qmin4 = (D.qual_min & 0xFFu) * 0x01010101u;
+        const unsigned gmask = D.qual_min <= 0xFFu ? 0xFFFFFFFFu : 0u;
+        const unsigned pw = (unsigned)(pos - P0);
+        u64 c[2], rc[2], inv = 0, hq = 0;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          u64 cc = 0, qq = 0;
+#pragma unroll 2
+          for (int g = 0; g < 8; ++g) {
+            const unsigned pg = pw + 32u * half + 4u * g;
+            while (rd < nrd && pg >= snext) snext = pack_next_start(off, o0, P0, nr, r0 + ++rd);
+            unsigned f8 = 0, r8 = 0, i4 = 0, h4 = 0;
+            const unsigned bi = pg - rd;  // staged byte of position pg, if it is a base
+            if (rd < nrd && pg + 4u < snext && bi + 4u <= nb) {
+              pack_group4(load4(sw, lead + bi), load4(qw, leadq + bi), qmin4, gmask, f8, r8, i4, h4);
+            } else {
+              for (unsigned i = 0; i < 4; ++i) {
+                const unsigned p = pg + i;
+                while (rd < nrd && p >= snext) snext = pack_next_start(off, o0, P0, nr, r0 + ++rd);
+                unsigned code = 0, valid = 0, good = 0;
+                const unsigned b = p - rd;
+                if (rd < nrd && p + 1u != snext && b < nb) {
+                  const unsigned ch = s_seq[lead + b];
+                  const unsigned u = (ch & 0xDFu) - 0x40u;  // A C G T (either case) -> bits 1 3 7 20
+                  valid = u < 32u ? (0x10008Au >> u) & 1u : 0u;
+                  code = valid ? ((ch >> 1) ^ (ch >> 2)) & 3u : 0u;  // A0 C1 G2 T3
+                  good = valid && (unsigned)s_qual[leadq + b] >= D.qual_min;
+                }
+                f8 |= code << (6u - 2u * i);
+                r8 |= (~code & 3u) << (2u * i);
+                i4 |= (valid ^ 1u) << (3u - i);
+                h4 |= good << (3u - i);
+              }
+            }
+            cc = (cc << 8) | f8;                // first position ends in the top bits
+            qq = (qq >> 8) | ((u64)r8 << 56);   // first position ends in the low bits
+            inv = (inv << 4) | i4;
+            hq = (hq << 4) | h4;
+          }
+          c[half] = cc;
+          rc[half] = qq;
         }
-        const unsigned m1 = __ballot_sync(0xffffffffu, code >> 1);
-        const unsigned m0 = __ballot_sync(0xffffffffu, code & 1u);
-        const unsigned mi = __ballot_sync(0xffffffffu, !valid);
-        const unsigned mh = __ballot_sync(0xffffffffu, good);
-        if (lane == 0) bal[it] = make_uint4(m1, m0, mi, mh);
-      }
-      __syncwarp();
-      if (w0 + threadIdx.x < w1) {  // lane j assembles word j from its two 32-position halves
-        const uint4 a = bal[2 * lane], b = bal[2 * lane + 1];
-        const u64 c0 = (spread_bits(__brev(a.x)) << 1) | spread_bits(__brev(a.y));
-        const u64 c1 = (spread_bits(__brev(b.x)) << 1) | spread_bits(__brev(b.y));
-        const u64 q0 = (spread_bits(~a.x) << 1) | spread_bits(~a.y);
-        const u64 q1 = (spread_bits(~b.x) << 1) | spread_bits(~b.y);
-        reinterpret_cast<ulonglong2*>(D.codes)[gw] = make_ulonglong2(c0, c1);
-        reinterpret_cast<ulonglong2*>(D.rcodes)[gw] = make_ulonglong2(q0, q1);
-        D.inv[gw] = ((u64)__brev(a.z) << 32) | __brev(b.z);
-        D.hq[gw] = ((u64)__brev(a.w) << 32) | __brev(b.w);
+        reinterpret_cast<ulonglong2*>(D.codes)[gw] = make_ulonglong2(c[0], c[1]);
+        reinterpret_cast<ulonglong2*>(D.rcodes)[gw] = make_ulonglong2(rc[0], rc[1]);
+        D.inv[gw] = inv;
+        D.hq[gw] = hq;
       }
     } else if (w0 + threadIdx.x < w1) {
       reinterpret_cast<ulonglong2*>(D.codes)[gw] = make_ulonglong2(0, 0);
