@@ -1,6 +1,6 @@
 """bench.py's GPU-only code paths cannot run here; this checks statically that every name a
 function reads is bound somewhere (a parameter, an assignment, an import, a module-level
-definition or a builtin), so a stale variable fails on the CPU instead of on the GPU machine."""
+definition or a builtin), so a stale variable fails without a GPU instead of when the path runs."""
 import ast
 import builtins
 import os
