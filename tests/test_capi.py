@@ -188,3 +188,15 @@ def test_hll_host_estimate_matches_oracle(lib):
     r = np.zeros(1 << 14, np.uint8)
     assert lib.kmer_analysis_hll_estimate(r.ctypes.data, 3, ctypes.byref(out)) == capi.KMA_EINVAL
     assert lib.kmer_analysis_hll_estimate(r.ctypes.data, 15, ctypes.byref(out)) == capi.KMA_EINVAL
+
+
+def test_host_result_buffers_layout():
+    """Host arrays for finalize_to_host have kma_result's layout (keys[c][2] u64, counts[c]
+    u32, ext[c][8] u32, codes[c][2] u8), C-contiguous."""
+    from paper_1705_11147_gb300 import host_result_buffers
+    keys, counts, ext, codes = host_result_buffers(5)
+    assert keys.shape == (5, 2) and keys.dtype == np.uint64
+    assert counts.shape == (5,) and counts.dtype == np.uint32
+    assert ext.shape == (5, 8) and ext.dtype == np.uint32
+    assert codes.shape == (5, 2) and codes.dtype == np.uint8
+    assert all(a.flags.c_contiguous for a in (keys, counts, ext, codes))
