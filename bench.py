@@ -588,6 +588,15 @@ def run_batched(args, ws, rank, local):
 
 # ------------------------------------------------------------------ served (job stream)
 
+def records_equal(a, b) -> bool:
+    """Two results hold the same records (keys, counts, extension counters, side codes),
+    compared after sorting by key."""
+    if len(a) != len(b):
+        return False
+    a, b = a.sorted(), b.sorted()
+    return all(np.array_equal(getattr(a, f), getattr(b, f)) for f in ("keys", "counts", "ext", "codes"))
+
+
 def run_served(args, ws, rank, local):
     """Counting jobs (genome log-U[1, 50] Mbp x scale, 30x of 150 bp, k in {31, 51}) through the
     continuous-batching server: saturation throughput with every job released at once against
@@ -621,7 +630,7 @@ def run_served(args, ws, rank, local):
     res_plain = run_plain(jobs)
     t_plain = time.perf_counter() - t0
     windows = sum(int(r.valid_windows) for r in res_srv)
-    same = all(len(a) == len(b) for a, b in zip(res_srv, res_plain))
+    same = all(records_equal(a, b) for a, b in zip(res_srv, res_plain))
     # latency under Poisson arrivals (arrival times of the first jobs, in real time)
     n_lat = min(len(jobs), args.latency_jobs)
     with Server(max_batch=args.max_batch, workers=args.workers) as srv:

@@ -296,8 +296,10 @@ int kmer_analysis_fetch_result(kma_handle* h, kma_result* out);
  * qual_offset are used; the sizing and launch-shape fields are ignored.
  * Limits: n_bases <= KMA_NOALLOC_MAX_BASES and n_reads <= KMA_NOALLOC_MAX_READS, otherwise
  * KMA_ETOOLARGE and nothing runs. The call synchronises `cuda_stream` before it returns.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any CUDA stream capture. All calls share the array and it keeps
+ * Every call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress), so the address stays right after a device reset. Device offsets
+ * must not decrease; decreasing ones are not fully checked on the device and can give wrong
+ * records instead of KMA_EINVAL. All calls share the array and it keeps
  * the previous call's contents (each call clears what it needs): calls whose GPU work can
  * overlap, on different streams or from unsynchronised threads, race on it. */
 #define KMA_NOALLOC_MAX_BASES 262144

@@ -40,6 +40,8 @@ def _lib():
         p, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
         lib.oracle_run.argtypes = [p, p, p, u64, ctypes.POINTER(_Params), u32, u32, ctypes.c_int]
         lib.oracle_run.restype = p
+        lib.oracle_run_parts.argtypes = [p, p, p, u64, ctypes.POINTER(_Params), p, u32, ctypes.c_int]
+        lib.oracle_run_parts.restype = p
         lib.oracle_size.argtypes = [p]
         lib.oracle_size.restype = u64
         lib.oracle_valid_windows.argtypes = [p]
@@ -106,7 +108,10 @@ class _Handle:
 def run(seq: np.ndarray, qual: np.ndarray, offsets: np.ndarray, k: int, min_depth: int = 2,
         min_ext_count: int = 2, qual_threshold: int = 20, qual_offset: int = 33,
         canonical: bool = True, part: int = 0, n_parts: int = 1, threads: int | None = None,
-        keep_table: bool = False) -> OracleResult:
+        keep_table: bool = False, parts=None) -> OracleResult:
+    """Records of the read set. With n_parts > 1 only the keys of owner partition `part` are
+    kept, or, if `parts` (an iterable of partition ids) is given, the keys of those partitions
+    (one scan of the reads for the whole set)."""
     seq = np.ascontiguousarray(seq, dtype=np.uint8)
     qual = np.ascontiguousarray(qual, dtype=np.uint8)
     offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
@@ -114,8 +119,14 @@ def run(seq: np.ndarray, qual: np.ndarray, offsets: np.ndarray, k: int, min_dept
     prm = _Params(k, min_depth, min_ext_count, qual_threshold, qual_offset, int(bool(canonical)))
     threads = threads or min(16, os.cpu_count() or 1)
     lib = _lib()
-    h = lib.oracle_run(seq.ctypes.data, qual.ctypes.data, offsets.ctypes.data, n_reads,
-                       ctypes.byref(prm), part, n_parts, threads)
+    if parts is not None and n_parts > 1:
+        keep = np.zeros(n_parts, np.uint8)
+        keep[np.asarray(list(parts), dtype=np.int64)] = 1
+        h = lib.oracle_run_parts(seq.ctypes.data, qual.ctypes.data, offsets.ctypes.data, n_reads,
+                                 ctypes.byref(prm), keep.ctypes.data, n_parts, threads)
+    else:
+        h = lib.oracle_run(seq.ctypes.data, qual.ctypes.data, offsets.ctypes.data, n_reads,
+                           ctypes.byref(prm), part, n_parts, threads)
     handle = _Handle(h)
     n = lib.oracle_size(h)
     keys = np.zeros((n, 2), np.uint64)
@@ -128,12 +139,12 @@ def run(seq: np.ndarray, qual: np.ndarray, offsets: np.ndarray, k: int, min_dept
 
 
 def run_readset(rs, threads: int | None = None, part: int = 0, n_parts: int = 1,
-                keep_table: bool = False, **overrides) -> OracleResult:
+                keep_table: bool = False, parts=None, **overrides) -> OracleResult:
     p = dict(rs.meta.get("params", {}))
     p.pop("bloom_fpr", None)
     p.update(overrides)
     return run(rs.seq, rs.qual, rs.offsets, threads=threads, part=part, n_parts=n_parts,
-               keep_table=keep_table, **p)
+               keep_table=keep_table, parts=parts, **p)
 
 
 def partition_of(keys: np.ndarray, k: int, n_parts: int) -> np.ndarray:

@@ -25,8 +25,9 @@
 //     Section 4.1) if |H| = 0 and F (fork, excluded from contigs, Section 2) if |H| >= 2.
 //     Unique-extension (UU, Section 5.2) k-mers have A/C/G/T on both sides.
 //  7. Owner-computes partitioning (Section 5.1: a fixed k-mer -> owner map): with n_parts > 1
-//     only keys with fnv1a(key string) mod n_parts == part are kept; the union over all parts
-//     equals the whole result. The FNV-1a hash here is the oracle's own.
+//     only keys with fnv1a(key string) mod n_parts == part are kept (or, with a set of parts,
+//     keys whose part is in the set); the union over all parts equals the whole result. The
+//     FNV-1a hash here is the oracle's own.
 //
 // Output: records sorted by key; key = 2-bit codes A0 C1 G2 T3, first base most
 // significant, as a 128-bit number split into (lo, hi) 64-bit words.
@@ -165,8 +166,9 @@ uint64_t fnv1a_chars(const char* s, int64_t n) {
 // Steps 1-4 over reads [r0, r1) into map m; returns the number of valid windows seen
 // (before partition filtering). Windows and their reverse complements are built in
 // fixed-size character buffers (k <= 63), so no step allocates per window.
+// keep[i] != 0: keys of owner partition i (of n_parts) are counted.
 uint64_t count_reads(const uint8_t* seq, const uint8_t* qual, const uint64_t* offsets,
-                     uint64_t r0, uint64_t r1, const Params& p, uint32_t part,
+                     uint64_t r0, uint64_t r1, const Params& p, const uint8_t* keep,
                      uint32_t n_parts, Map& m) {
   uint64_t valid_windows = 0;
   const int64_t k = p.k;
@@ -189,7 +191,7 @@ uint64_t count_reads(const uint8_t* seq, const uint8_t* qual, const uint64_t* of
       for (int64_t j = 0; j < k; ++j) rc[j] = complement(w[k - 1 - j]);
       const bool forward = !p.canonical || std::memcmp(w, rc, (size_t)k) <= 0;
       const char* key = forward ? w : rc;
-      if (n_parts > 1 && fnv1a_chars(key, k) % n_parts != part) continue;
+      if (n_parts > 1 && !keep[fnv1a_chars(key, k) % n_parts]) continue;
       Rec& rec = m[pack_chars(key, k)];
       rec.count += 1;
       const bool left_ok = usable(s, q, i - 1, p);
@@ -241,12 +243,15 @@ typedef struct {
   uint32_t k, min_depth, min_ext_count, qual_threshold, qual_offset, canonical;
 } oracle_params;
 
-void* oracle_run(const uint8_t* seq, const uint8_t* qual, const uint64_t* offsets,
-                 uint64_t n_reads, const oracle_params* op, uint32_t part, uint32_t n_parts,
-                 int n_threads) {
+// keep[0 .. n_parts): which owner partitions to count (NULL or n_parts <= 1: all keys).
+void* oracle_run_parts(const uint8_t* seq, const uint8_t* qual, const uint64_t* offsets,
+                       uint64_t n_reads, const oracle_params* op, const uint8_t* keep_in,
+                       uint32_t n_parts, int n_threads) {
   Params p{op->k, op->min_depth, op->min_ext_count, op->qual_threshold, op->qual_offset,
            op->canonical};
-  if (n_parts == 0) n_parts = 1;
+  if (n_parts == 0 || !keep_in) n_parts = 1;
+  const std::vector<uint8_t> keep(keep_in && n_parts > 1 ? keep_in : nullptr,
+                                  keep_in && n_parts > 1 ? keep_in + n_parts : nullptr);
   if (n_threads < 1) n_threads = 1;
   const size_t T = (size_t)n_threads;
   // 1. each thread counts the windows of its share of the reads (steps 1-4)
@@ -257,7 +262,7 @@ void* oracle_run(const uint8_t* seq, const uint8_t* qual, const uint64_t* offset
     for (size_t t = 0; t < T; ++t) {
       const uint64_t r0 = n_reads * t / T, r1 = n_reads * (t + 1) / T;
       th.emplace_back([&, t, r0, r1] {
-        windows[t] = count_reads(seq, qual, offsets, r0, r1, p, part, n_parts, *maps[t].map);
+        windows[t] = count_reads(seq, qual, offsets, r0, r1, p, keep.data(), n_parts, *maps[t].map);
       });
     }
     for (auto& x : th) x.join();
@@ -300,6 +305,16 @@ void* oracle_run(const uint8_t* seq, const uint8_t* qual, const uint64_t* offset
   res->recs.reserve(all.size());
   for (auto& kv : all) res->keys.push_back(kv.first), res->recs.push_back(kv.second);
   return res;
+}
+
+// One owner partition `part` of n_parts (n_parts <= 1: every key).
+void* oracle_run(const uint8_t* seq, const uint8_t* qual, const uint64_t* offsets,
+                 uint64_t n_reads, const oracle_params* op, uint32_t part, uint32_t n_parts,
+                 int n_threads) {
+  if (n_parts <= 1) return oracle_run_parts(seq, qual, offsets, n_reads, op, nullptr, 1, n_threads);
+  std::vector<uint8_t> keep(n_parts, 0);
+  if (part < n_parts) keep[part] = 1;
+  return oracle_run_parts(seq, qual, offsets, n_reads, op, keep.data(), n_parts, n_threads);
 }
 
 uint64_t oracle_size(void* h) { return ((Result*)h)->keys.size(); }

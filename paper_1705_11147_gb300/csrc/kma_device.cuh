@@ -164,6 +164,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned phase, 
   return false;
 }
 
+// After a wait that gave up: before the CTA may exit, the bulk copies already issued into its
+// shared memory must land. Waits up to 64 times the first limit (still bounded; copies that
+// have not landed by then are reported by the flag the caller already raised).
+__device__ __forceinline__ bool mbar_drain(unsigned bar, unsigned phase, unsigned limit) {
+  for (unsigned r = 0; r < 64; ++r)
+    if (mbar_wait_bounded(bar, phase, limit)) return true;
+  return false;
+}
+
 // ------------------------------------------------------------------ 2-bit words
 
 // Reverse the order of the 32 two-bit groups of x.

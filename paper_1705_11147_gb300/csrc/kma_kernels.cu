@@ -175,13 +175,16 @@ __device__ __forceinline__ int find_pack_sample(const PackBatch& B, u64 c) {
 // Last read r with start ps_r = offsets[r] - o0 + r <= p, found by a warp: the answer lies in [lo, hi) and offsets[lo] - o0 + lo <= p;
 // each round the 32 lanes test 32 evenly spaced reads, so ~log32(hi - lo) dependent loads
 // instead of log2. Called by all lanes of a warp with the same arguments; all return it.
-__device__ __forceinline__ u64 read_at_warp(const u64* off, u64 o0, u64 lo, u64 hi, u64 p) {
+// With non-decreasing offsets the lanes that qualify are a prefix of the warp; `bad` is set
+// when they are not (decreasing offsets), and the caller reports it.
+__device__ __forceinline__ u64 read_at_warp(const u64* off, u64 o0, u64 lo, u64 hi, u64 p, bool& bad) {
   const unsigned lane = threadIdx.x & 31;
   while (hi - lo > 1) {
     const u64 step = (hi - lo + 31) / 32;
     const u64 idx = lo + lane * step;
     const bool le = idx < hi && off[idx] - o0 + idx <= p;  // a prefix of the lanes (starts increase)
     const unsigned m = __ballot_sync(0xffffffffu, le);
+    bad |= (m & (m + 1u)) != 0u;
     const u64 nlo = m ? lo + (u64)(31 - __clz(m)) * step : lo;
     hi = nlo + step < hi ? nlo + step : hi;
     lo = nlo;
@@ -192,18 +195,20 @@ __device__ __forceinline__ u64 read_at_warp(const u64* off, u64 o0, u64 lo, u64 
 // Same answer as read_at_warp, trying first the 32 reads around `guess` in one round of
 // loads: with reads of similar length a proportional guess lands within a few reads, which
 // saves the ~log32(hi - lo) dependent rounds of a search over all the batch's reads.
-__device__ __forceinline__ u64 read_at_warp_near(const u64* off, u64 o0, u64 lo, u64 hi, u64 p, u64 guess) {
+__device__ __forceinline__ u64 read_at_warp_near(const u64* off, u64 o0, u64 lo, u64 hi, u64 p, u64 guess,
+                                                 bool& bad) {
   if (hi - lo > 32) {
     const unsigned lane = threadIdx.x & 31;
     u64 g0 = guess > lo + 16 ? guess - 16 : lo;
     if (g0 > hi - 32) g0 = hi - 32;
     const u64 idx = g0 + lane;  // inside [lo, hi)
     const unsigned m = __ballot_sync(0xffffffffu, off[idx] - o0 + idx <= p);  // a prefix of the lanes
+    bad |= (m & (m + 1u)) != 0u;
     // the last read starting at or before p is inside the window: its first read qualifies and
     // a later one does not (or the window ends at hi)
     if ((m & 1u) && (m != 0xffffffffu || g0 + 32 == hi)) return g0 + (u64)(31 - __clz(m));
   }
-  return read_at_warp(off, o0, lo, hi, p);
+  return read_at_warp(off, o0, lo, hi, p, bad);
 }
 
 // Batch-relative index of the first base at or after arena position p (clamped to n_bases),
@@ -298,7 +303,9 @@ __global__ void __launch_bounds__(kPackThreads, 4) pack_kernel(const __grid_cons
       u64 r = 0, b = 0;
       if (D.n_reads) {
         const u64 guess = (u64)((double)p * (double)D.n_reads / (double)(D.n_bases + D.n_reads));
-        r = read_at_warp_near(off, o0, 0, D.n_reads, p, guess);
+        bool bad = false;
+        r = read_at_warp_near(off, o0, 0, D.n_reads, p, guess, bad);
+        if (bad && (threadIdx.x & 31) == 0) atomicOr(&D.status->flags, kFlagBadOffsets);
         b = base_at_or_after(D, o0, r, p);
       }
       if ((threadIdx.x & 31) == 0) {
@@ -350,12 +357,15 @@ __global__ void __launch_bounds__(kPackThreads, 4) pack_kernel(const __grid_cons
         phase ^= 1u;
       } else {
         atomicOr(&D.status->flags, kFlagTimeout);
-        if (!B.skip_copy) mbar_wait_bounded(bar, phase, B.wait_limit);  // copies may still land
+        if (!B.skip_copy) mbar_drain(bar, phase, B.wait_limit);  // copies may still land
         s_ok = 2;
       }
     }
     __syncthreads();
     if (s_ok == 2) return;  // uniform: the chunk's input never arrived
+    // the chunk's reads must not decrease (device offsets are not checked on the host)
+    for (u64 r = s_r0 + threadIdx.x; r < s_r1 && r < D.n_reads; r += kPackThreads)
+      if (off[r + 1] < off[r]) atomicOr(&D.status->flags, kFlagBadOffsets);
     const unsigned nb = (unsigned)(s_b1 - s_b0);  // staged bases
     const unsigned lead = s_lead & 0xFF, leadq = s_lead >> 8;
     const u64 ww0 = w0 + warp * 32;                  // first word of this warp
@@ -365,7 +375,9 @@ __global__ void __launch_bounds__(kPackThreads, 4) pack_kernel(const __grid_cons
       // position p has batch base index p - r; the chunk's staged bytes start at the base of
       // the chunk's first position, so its byte offset is (p - P0) - (r - r0).
       const u64 nr = D.n_reads, P0 = w0 * 64, r0 = s_r0;
-      const u64 rw = nr ? read_at_warp(off, o0, s_r0, s_r1 + 1, ww0 * 64) : 0;
+      bool bad = false;
+      const u64 rw = nr ? read_at_warp(off, o0, s_r0, s_r1 + 1, ww0 * 64, bad) : 0;
+      if (bad && (threadIdx.x & 31) == 0) atomicOr(&D.status->flags, kFlagBadOffsets);
       if (w0 + threadIdx.x < w1) {
         // the read holding this word's first position (binary search from the warp's read)
         const u64 pos = (w0 + threadIdx.x) * 64;

@@ -18,7 +18,6 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "../../include/kmer_analysis.h"
 #include "kma_internal.cuh"
@@ -48,27 +47,20 @@ constexpr u64 kOffTable = kOffStatus + kStatusBytes;
 constexpr u64 kNoallocScratchBytes = kOffTable + kTableBytes;
 
 // The scratch array. In host code `g_noalloc_scratch` is only a stand-in symbol, not a device
-// address: kernels get the address from cudaGetSymbolAddress (set_up below).
+// address: kernels get the address from cudaGetSymbolAddress (scratch_address below).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-std::mutex g_mu;
-unsigned char* g_scratch_ptr[64];
-bool g_scratch_ready[64];
-
-// Once per device, with that device current: look up the device address of the array.
-int set_up(int dev, unsigned char** out) {
-  if (dev < 0 || dev >= 64) return KMA_EINVAL;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ready[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
-      cudaGetLastError();
-      return KMA_ECUDA;
-    }
-    g_scratch_ptr[dev] = static_cast<unsigned char*>(ptr);
-    g_scratch_ready[dev] = true;
+// The device address of the array in the current device's context. It is looked up on every
+// call: a cached address would go stale if the process reset the device (cudaDeviceReset) or
+// otherwise made a new context, where the module, and the array with it, is loaded anew. The
+// lookup is a host-side query and the call synchronises with its stream anyway.
+int scratch_address(unsigned char** out) {
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
+    cudaGetLastError();
+    return KMA_ECUDA;
   }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<unsigned char*>(ptr);
   return KMA_OK;
 }
 
@@ -98,7 +90,7 @@ extern "C" int kmer_analysis_count_small_noalloc(const kma_params* params, const
   if ((rc = check(cudaGetDevice(&dev)))) return rc;
   if ((rc = check(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev)))) return rc;
   unsigned char* base = nullptr;
-  if ((rc = set_up(dev, &base))) return rc;
+  if ((rc = scratch_address(&base))) return rc;
 
   u64* d_codes = reinterpret_cast<u64*>(base + kOffCodes);
   u64* d_rcodes = reinterpret_cast<u64*>(base + kOffRcodes);

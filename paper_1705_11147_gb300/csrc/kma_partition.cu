@@ -304,8 +304,8 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
     if (!ok) {  // give up: report, let the copies in flight land (bounded), stop the warp
       if (lane == 0) {
         atomicOr(&G.status->flags, kFlagTimeout);
-        mbar_wait_bounded(bar, (phases >> buf) & 1u, G.wait_limit);
-        if (tn < n_tiles) mbar_wait_bounded(smem_u32(&S.bar[buf ^ 1]), (phases >> (buf ^ 1)) & 1u, G.wait_limit);
+        mbar_drain(bar, (phases >> buf) & 1u, G.wait_limit);
+        if (tn < n_tiles) mbar_drain(smem_u32(&S.bar[buf ^ 1]), (phases >> (buf ^ 1)) & 1u, G.wait_limit);
       }
       return;
     }

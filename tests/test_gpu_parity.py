@@ -379,19 +379,33 @@ def test_batch_graph_replay_equals_solo(gpu):
 
 # ------------------------------------------------------------------ full-size sampled parity
 
+def _owner_subset(res, k, n_parts, parts):
+    """The records of `res` whose key belongs to one of the oracle's owner partitions `parts`
+    (of n_parts, the oracle's own hash)."""
+    sel = np.isin(oracle.partition_of(res.keys, k, n_parts), list(parts))
+    return type(res)(res.keys[sel], res.counts[sel], res.ext[sel], res.codes[sel]).sorted()
+
+
 @pytest.mark.slow
-def test_large_200m_sampled_partition(gpu):
-    """6 Gbases, 4.8 G windows: the whole GPU result is checked on the k-mers of one owner
-    partition (1/256 of the key space, by the oracle's own hash), computed by the oracle
-    one partition at a time, plus the total window count."""
+def test_large_200m_sampled_partitions(gpu):
+    """6 Gbases, 4.8 G windows, in the bench's launch configuration: the whole GPU result is
+    checked on the k-mers of 16 of 256 owner partitions (by the oracle's own hash), computed
+    by the oracle in one scan of the reads. The set holds the partitions of the eight most
+    frequent k-mers of the result (repeats, the keys with the most contended counters) and
+    the first partitions up to 16. The total window count is checked too."""
     import bench
     rs = synth.workload("large_200m")
     got = bench.run_large_once(rs)
-    part, n_parts = 0, 256
-    sel = oracle.partition_of(got.keys, 51, n_parts) == part
-    sub = type(got)(got.keys[sel], got.counts[sel], got.ext[sel], got.codes[sel])
-    want = oracle.run_readset(rs, part=part, n_parts=n_parts)
-    assert_same(sub.sorted(), want, "large_200m partition 0/256")
+    n_parts = 256
+    top = np.argsort(got.counts)[-8:]
+    parts = set(int(x) for x in oracle.partition_of(got.keys[top], 51, n_parts))
+    x = 0
+    while len(parts) < 16:
+        parts.add(x)
+        x += 1
+    want = oracle.run_readset(rs, n_parts=n_parts, parts=sorted(parts))
+    assert len(want) > 10_000_000
+    assert_same(_owner_subset(got, 51, n_parts, parts), want, f"large_200m partitions {sorted(parts)}/256")
     assert got.valid_windows == want.valid_windows
 
 
@@ -684,29 +698,39 @@ def test_finalize_to_host_overflow_capacity_and_query(gpu):
 
 @pytest.mark.slow
 def test_batched_64_every_sample_vs_oracle(gpu):
-    """All 64 samples of the batched workload (genome sizes scaled to 0.5 %, the rest of the
-    recipe unchanged) through one captured graph, the bench's batched path: every sample's
-    records equal the oracle's."""
-    from paper_1705_11147_gb300 import BatchGraph, KmerAnalysis, make_params
-    sets = [synth.sample_reads(s) for s in synth.batched_specs(64, scale=0.005)]
-    handles = [KmerAnalysis(make_params(k=51, min_depth=2, qual_threshold=20, max_bases=rs.n_bases,
-                                        max_reads=rs.n_reads, expected_distinct=rs.n_bases,
-                                        partitions=1 if i % 4 else 3))
-               for i, rs in enumerate(sets)]
+    """All 64 samples of the batched workload at the bench's size (12.7 Gbases), with the
+    bench's per-sample parameters, through one captured graph replayed once: every sample's
+    records equal the oracle's on one owner partition of 32 (by the oracle's own hash), and
+    every sample's window count equals the oracle's."""
+    import bench
+    from paper_1705_11147_gb300 import BatchGraph, KmerAnalysis
+    gpu.cuda.empty_cache()
+    sets = [synth.sample_reads(s) for s in synth.batched_specs(64, scale=1.0)]
+    handles = [KmerAnalysis(bench.make_handle_params(rs)) for rs in sets]
     g = BatchGraph(handles, [to_dev(gpu, rs) for rs in sets])
     g.replay()
-    g.results()
-    for i, (h, rs) in enumerate(zip(handles, sets)):
-        assert_same(h.copy_result().sorted(), oracle.run_readset(rs), f"sample {i}")
+    infos = g.results()
+    results = []
+    for h in handles:
+        results.append(h.copy_result())
         h.destroy()
+    del g, handles
+    gpu.cuda.empty_cache()
+    for i, (res, info, rs) in enumerate(zip(results, infos, sets)):
+        want = oracle.run_readset(rs, n_parts=32, parts=[i % 32])
+        assert_same(_owner_subset(res, 51, 32, [i % 32]), want, f"sample {i}")
+        assert info.valid_windows == want.valid_windows
 
 
 @pytest.mark.slow
 def test_served_subset_vs_oracle(gpu):
-    """30 jobs of the served workload (genomes scaled to 0.2 %), the smallest and the largest
-    of all 500 among them, through the batching server: every job equals the oracle."""
+    """30 jobs of the served workload at the bench's scale (genomes log-U[1, 50] Mbp x 0.05),
+    the smallest and the largest of all 500 among them, through the batching server with the
+    bench's per-job parameters: every job equals the oracle on 4 of 16 owner partitions (by
+    the oracle's own hash); the window counts are checked whole."""
+    import bench
     from paper_1705_11147_gb300.serve import Job, Server
-    specs = synth.served_specs(500, scale=0.002)
+    specs = synth.served_specs(500, scale=0.05)
     by_size = sorted(range(len(specs)), key=lambda j: specs[j]["G"])
     pick = {by_size[0], by_size[-1]}
     j = 0
@@ -718,12 +742,40 @@ def test_served_subset_vs_oracle(gpu):
     for i in pick:
         rs = synth.sample_reads(specs[i])
         p = dict(rs.meta["params"])
-        p.pop("bloom_fpr")
-        p["expected_distinct"] = rs.n_bases
+        p.pop("bloom_fpr", None)
+        p.update(bench.workload_sizing(rs))
         jobs.append(Job(rs.seq, rs.qual, rs.offsets, params=p, job_id=i))
         sets.append(rs)
     assert len(jobs) == 30 and {j.params["k"] for j in jobs} == {31, 51}
     with Server(max_batch=8, workers=2) as srv:
-        got = [f.result(timeout=600) for f in [srv.submit(j) for j in jobs]]
+        got = [f.result(timeout=900) for f in [srv.submit(j) for j in jobs]]
     for i, (res, rs) in enumerate(zip(got, sets)):
-        assert_same(res.sorted(), oracle.run_readset(rs), f"job {pick[i]}")
+        k = rs.meta["params"]["k"]
+        parts = [(4 * i + d) % 16 for d in range(4)]
+        want = oracle.run_readset(rs, n_parts=16, parts=parts)
+        assert_same(_owner_subset(res, k, 16, parts), want, f"job {pick[i]}")
+        assert res.valid_windows == want.valid_windows
+
+
+# ------------------------------------------------------------------ multi-GPU owner shards
+
+@pytest.mark.parametrize("n_parts", [2, 3])
+@pytest.mark.parametrize("mode", ["one_table", "partitioned", "host_chunks", "one_table_no_bloom"])
+def test_owner_shards_union_to_whole(gpu, plain, n_parts, mode):
+    """Multi-GPU owner-computes (Section 5.1), one shard at a time on this GPU: each handle
+    counts only the k-mers its n_parts/part selects. The shards are disjoint, their union is
+    the oracle's whole result, and their window counts add up to the whole's."""
+    rs, want = plain
+    opts = {"one_table": dict(partitions=1),
+            "partitioned": dict(partitions=7),
+            "host_chunks": dict(partitions=5, device_inputs=False, staging_bytes=2 << 20),
+            "one_table_no_bloom": dict(partitions=1, use_bloom=False)}[mode]
+    shards = [run_gpu(gpu, rs, n_parts=n_parts, part=part, **opts) for part in range(n_parts)]
+    assert all(len(s) > 0 for s in shards)
+    keys = np.concatenate([s.keys for s in shards])
+    assert len(np.unique(keys, axis=0)) == len(keys), "shards overlap"
+    merged = type(shards[0])(keys, np.concatenate([s.counts for s in shards]),
+                             np.concatenate([s.ext for s in shards]),
+                             np.concatenate([s.codes for s in shards])).sorted()
+    assert_same(merged, want, f"union of {n_parts} shards ({mode})")
+    assert sum(s.valid_windows for s in shards) == want.valid_windows

@@ -244,6 +244,26 @@ def test_partition_union_equals_whole(small_set):
         assert (oracle.partition_of(p.keys, 51, 5) == i).all()
 
 
+def test_partition_set_equals_selected_parts(small_set):
+    """A set of owner partitions in one scan (used to check full-size GPU runs on many
+    partitions at once) keeps exactly the whole result's keys whose owner is in the set, with
+    their records unchanged; the set and its complement are disjoint and cover the whole."""
+    whole = oracle.run_readset(small_set)
+    owner = oracle.partition_of(whole.keys, 51, 7)
+    chosen = [0, 3, 4]
+    got = oracle.run_readset(small_set, n_parts=7, parts=chosen)
+    rest = oracle.run_readset(small_set, n_parts=7, parts=[1, 2, 5, 6])
+    sel = np.isin(owner, chosen)
+    assert 0 < len(got) < len(whole) and len(got) + len(rest) == len(whole)
+    for f in ("keys", "counts", "ext", "codes"):
+        np.testing.assert_array_equal(getattr(got, f), getattr(whole, f)[sel])
+        np.testing.assert_array_equal(getattr(rest, f), getattr(whole, f)[~sel])
+    assert got.valid_windows == whole.valid_windows
+    # one part given as a set is that part
+    one = oracle.run_readset(small_set, n_parts=7, parts=[5])
+    np.testing.assert_array_equal(one.keys, oracle.run_readset(small_set, part=5, n_parts=7).keys)
+
+
 def test_threads_do_not_change_result(small_set):
     a = oracle.run_readset(small_set, threads=1)
     b = oracle.run_readset(small_set, threads=7)

@@ -99,6 +99,61 @@ def test_noalloc_matches_regular_path_two_calls(torch_cuda):
     _same(reg_a, _noalloc(torch, a, len(reg_a), **pa))
 
 
+def _oracle_same(rs, got, **params):
+    import oracle
+    want = oracle.run(rs.seq, rs.qual, rs.offsets, k=params["k"], min_depth=params["min_depth"],
+                      min_ext_count=params["min_ext_count"], qual_threshold=params["qual_threshold"],
+                      canonical=params.get("canonical", True))
+    _same(want, got)
+
+
+def test_noalloc_at_the_limits_and_vs_oracle(torch_cuda):
+    """The sizes the fixed array is laid out for, used to the last byte, and the cases with no
+    work: exactly KMA_NOALLOC_MAX_BASES bases, exactly KMA_NOALLOC_MAX_READS (very short)
+    reads, an empty read set, forward-only keys. Each result equals the regular path's and the
+    oracle's."""
+    torch = torch_cuda
+    from paper_1705_11147_gb300 import capi
+    nb = capi.KMA_NOALLOC_MAX_BASES
+    # exactly the base limit, reads of 100-250 bases, k = 31
+    rs = synth.random_reads(seed=11, n_reads=2000, min_len=100, max_len=250, alphabet=b"ACGTACGTACGTN",
+                            q_lo=10, q_hi=40)
+    cut = int(np.searchsorted(rs.offsets, nb, side="right")) - 1
+    offs = rs.offsets[: cut + 1].copy()
+    offs = np.append(offs, nb).astype(np.uint64)
+    full = synth.ReadSet(rs.seq[:nb].copy(), rs.qual[:nb].copy(), offs)
+    full.seq[: nb // 2] = np.frombuffer((b"ACGTTGCAAC" * (nb // 20 + 1))[: nb // 2], np.uint8)
+    assert full.n_bases == nb
+    pa = dict(k=31, min_depth=2, min_ext_count=2, qual_threshold=20)
+    got = _noalloc(torch, full, nb, **pa)
+    _same(_regular(torch, full, **pa), got)
+    _oracle_same(full, got, **pa)
+    # exactly the read limit and the base limit at once: 262,143 reads of 0 or 1 base and one
+    # long read holding the rest, k = 1
+    lens = np.random.default_rng(3).integers(0, 2, capi.KMA_NOALLOC_MAX_READS)
+    lens[-1] = nb - int(lens[:-1].sum())
+    tot = int(lens.sum())
+    assert tot == nb
+    tiny = synth.random_reads(seed=12, n_reads=1, min_len=tot, max_len=tot, alphabet=b"ACGT", q_lo=15, q_hi=40)
+    offs = np.zeros(lens.size + 1, np.uint64)
+    offs[1:] = np.cumsum(lens)
+    tiny = synth.ReadSet(tiny.seq, tiny.qual, offs)
+    assert tiny.n_reads == capi.KMA_NOALLOC_MAX_READS and tiny.n_bases == nb
+    pt = dict(k=1, min_depth=1, min_ext_count=1, qual_threshold=20)
+    got = _noalloc(torch, tiny, 16, **pt)
+    _same(_regular(torch, tiny, use_bloom=False, **pt), got)
+    _oracle_same(tiny, got, **pt)
+    # forward-only keys (canonical = 0), even k allowed
+    pf = dict(k=20, min_depth=2, min_ext_count=1, qual_threshold=20, canonical=False)
+    got = _noalloc(torch, full, nb, **pf)
+    _same(_regular(torch, full, **pf), got)
+    _oracle_same(full, got, **pf)
+    # no reads at all: no records, and the array's previous contents do not show through
+    empty = synth.ReadSet(np.zeros(0, np.uint8), np.zeros(0, np.uint8), np.zeros(1, np.uint64))
+    rc, n, *_ = _noalloc(torch, empty, 8, **pa)
+    assert rc == 0 and n == 0
+
+
 def test_noalloc_limits_and_capacity(torch_cuda):
     torch = torch_cuda
     from paper_1705_11147_gb300 import capi
