@@ -205,56 +205,78 @@ def kernel_source_digest(files) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(summary: str, digest: str):
-    """DRAM bytes per unit recorded by an ncu capture (profiles/<summary>), or None when the
-    kernel sources changed since the capture."""
+def profiled_values(summary: str, digest: str) -> dict:
+    """Per-unit figures recorded by an ncu capture (profiles/<summary>: lines `name: value`),
+    or {} when the kernel sources changed since the capture."""
     try:
         text = open(os.path.join(PROFILE_DIR, summary)).read()
     except OSError:
-        return None
-    vals = dict(line.split(":", 1) for line in text.splitlines()
-                if line.startswith(("kernel_source_digest:", "dram_bytes_per_unit:")))
-    if vals.get("kernel_source_digest", "").strip() != digest:
-        return None
-    try:
-        return float(vals["dram_bytes_per_unit"])
-    except (KeyError, ValueError):
-        return None
+        return {}
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and not line.startswith((" ", "|", "#")):
+            key, val = line.split(":", 1)
+            vals[key.strip()] = val.strip()
+    if vals.get("kernel_source_digest", "").split(" ")[0] != digest:
+        return {}
+    out = {}
+    for key in ("dram_bytes_per_unit", "l2_requests_per_unit", "l2_peak_requests_per_s"):
+        try:
+            out[key] = float(vals[key].split(" ")[0])
+        except (KeyError, ValueError):
+            pass
+    return out
 
 
 def roofline(timing: dict, res_info, positions: int, peak_gbs: float, plan_used, k: int) -> dict:
-    """Dominant kernel, algorithmic DRAM bytes per launch (32-byte sectors; Bloom filter and
-    table far larger than L2):
-    one table (pass_kernel, Bloom mode):
+    """Dominant kernel (the counting pass), algorithmic DRAM bytes per launch.
+    one table (pass_kernel, Bloom mode; filter and table far larger than L2, 32-byte sectors):
       64 B per valid window (Bloom word sector read + write-back), 128 B per window whose k-mer
       the filter had seen (slot key/count sector + extension sector, read + written back),
       0.625 B per arena position (codes, reverse codes... read, marks written).
-    partitions (part_pass_kernel, Bloom mode):
-      per record (one per valid window) its key + info byte read (17 B, 9 B for k <= 32),
-      1 B per first sighting (flag written back), and each partition's Bloom sub-filter and
-      sub-table brought from HBM once and written back once: 2 x (filter + table bytes)."""
+    partitions (part_pass_kernel, Bloom mode), the partitioned model of the hot-path table:
+      per record (one per valid window) its key + info byte read (17 B, 9 B for k <= 32), and
+      per first sighting the record written back (compacted for the recount). A second figure
+      adds each partition's Bloom sub-filter and sub-table brought from HBM once and written
+      back once (2 x filter + table bytes).
+    The partitioned pass keeps its random atomics in L2, so its ceiling is the L2 request
+    rate: `l2` gives the L2 requests per record from the ncu capture times the records, over
+    the live kernel time, against the L2's peak request rate (slices x L2 clock, from ncu)."""
     W = int(res_info.valid_windows)
     F = int(timing["first_sightings"])
     ms = timing["ms_pass"] / max(timing["n_pass"], 1)
+    extra = {}
     if plan_used.partitions > 1:
         rec = (16 if k > 32 else 8) + 1
         struct_bytes = plan_used.bloom_words * 8 + plan_used.table_slots * 64
-        algo = float(W) * rec + F + 2.0 * struct_bytes
+        algo = float(W) * rec + float(F) * rec
         kernel, files, summary = ("part_pass_kernel (Bloom mode)", ["kma_partition.cu", "kma_device.cuh"],
                                   "part_pass_kernel_large_200m.md")
-        units = W
+        with_struct = algo + 2.0 * struct_bytes
+        extra["with_partition_structures"] = {
+            "algo_bytes_per_launch": int(with_struct),
+            "achieved": round(with_struct / (ms * 1e-3) / 1e9, 1),
+            "frac": round(with_struct / (ms * 1e-3) / 1e9 / peak_gbs, 4)}
     else:
         algo = 64.0 * W + 128.0 * (W - F) + 0.625 * positions
         kernel, files, summary = ("pass_kernel (Bloom mode)", ["kma_kernels.cu", "kma_device.cuh"],
                                   "pass_kernel_large_200m.md")
-        units = W
     achieved = algo / (ms * 1e-3) / 1e9
-    per_unit = profiled_traffic(summary, kernel_source_digest(files))
-    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs, "unit": "GB/s",
-            "frac": round(achieved / peak_gbs, 4),
-            "traffic": None if per_unit is None else int(per_unit * units),
-            "kernel": kernel, "ms_per_launch": round(ms, 3), "algo_bytes_per_launch": int(algo),
-            "peak_source": "of measured (hbm_gbs)"}
+    prof = profiled_values(summary, kernel_source_digest(files))
+    out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs, "unit": "GB/s",
+           "frac": round(achieved / peak_gbs, 4),
+           "traffic": int(prof["dram_bytes_per_unit"] * W) if "dram_bytes_per_unit" in prof else None,
+           "kernel": kernel, "ms_per_launch": round(ms, 3), "algo_bytes_per_launch": int(algo),
+           "peak_source": "of measured (hbm_gbs)", **extra}
+    if "l2_requests_per_unit" in prof and "l2_peak_requests_per_s" in prof:
+        req = prof["l2_requests_per_unit"] * W
+        l2_ach = req / (ms * 1e-3) / 1e9
+        l2_peak = prof["l2_peak_requests_per_s"] / 1e9
+        out["l2"] = {"achieved": round(l2_ach, 1), "peak": round(l2_peak, 1), "unit": "G L2 requests/s",
+                     "frac": round(l2_ach / l2_peak, 4), "requests_per_launch": int(req),
+                     "source": "ncu lts__t_requests per record x records / live kernel time; peak = "
+                               "lts__t_requests.sum.peak_sustained x L2 clock (ncu)"}
+    return out
 
 
 def load_peak() -> float:

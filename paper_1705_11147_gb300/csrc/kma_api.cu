@@ -185,7 +185,8 @@ int derive(const kma_params* p, Derived& d) {
   d.plan.device_bytes = 2 * d.codes_words * 8 + 2 * d.bit_words * 8 + d.mark_words * 4 +
                         d.plan.bloom_words * 8 + d.plan.table_slots * sizeof(Slot) +
                         sizeof(DevStatus) + 2 * (2 * d.staging + (d.staging / 16 + 2) * 8);
-  if (d.P > 1) d.plan.device_bytes += (p->max_bases + p->max_bases / 16) * d.rec_bytes + d.Wt * d.P * 8;
+  if (d.P > 1)  // record buckets and the key filter
+    d.plan.device_bytes += (p->max_bases + p->max_bases / 16) * d.rec_bytes + d.Wt * d.P * 8;
   return KMA_OK;
 }
 
@@ -453,7 +454,7 @@ PassDesc pass_desc(kma_handle* h, unsigned mode, u64 q0, u64 q1) {
 // for tests) copies that are never issued and a short limit, which must end in KMA_ETIMEOUT.
 void set_pack_waits(kma_handle* h, PackBatch& pb) {
   pb.skip_copy = h->p.fault_inject == 1 ? 1u : 0u;
-  pb.wait_limit = h->p.fault_inject == 1 ? (1u << 10) : (1u << 22);
+  pb.wait_limit = h->p.fault_inject == 1 ? kWaitPollsInjected : kWaitPolls;
 }
 
 // Reserve arena space for a batch and describe it for the pack kernel.
@@ -490,7 +491,7 @@ PartGeom part_geom(kma_handle* h) {
   g.n_parts = h->p.n_parts > 1 ? h->p.n_parts : 1;
   g.part = h->p.n_parts > 1 ? h->p.part : 0;
   g.rpt = h->p.windows_per_thread >= 4 ? 4 : 2;
-  g.wait_limit = 1u << 22;
+  g.wait_limit = kWaitPolls;
   g.no_overflow = h->count_bound < (1ull << 32) ? 1u : 0u;
   g.group = h->p.heavy_hitters ? 1u : 0u;
   return g;
@@ -512,23 +513,29 @@ int prepare_records(kma_handle* h, u64 n_pos, u64 n_reads, u64 n_bases, cudaStre
   u64 ocap = n_pos / 16 + 65536;
   if (P * cap < n_bases) ocap = std::max(ocap, n_bases - P * cap + n_pos / 64);
   ocap = (ocap + 15) & ~15ull;
-  if (cap >= (1ull << 32)) return KMA_EINVAL;  // more partitions needed for this batch size
+  // the kernels hold in-bucket and overflow positions, and tile numbers, in 32 bits
+  const u64 tile_recs = 32ull * part_geom(h).rpt;
+  if (cap >= (1ull << 32) || ocap >= (1ull << 32) ||
+      P * ((cap + tile_recs - 1) / tile_recs) + (ocap + tile_recs - 1) / tile_recs >= (1ull << 31))
+    return KMA_EINVAL;  // more partitions, or smaller count() batches, are needed
   h->count_bound += cap + ocap;
   const u64 total = P * cap + ocap;
   kma_handle::RecBatch rb{nullptr, nullptr, nullptr, cap, ocap};
   const size_t kb = (size_t)total * (k > 32 ? 16 : 8);
   cudaError_t e = cudaMallocFromPoolAsync(&rb.keys, kb, h->pool, st);
   if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&rb.info, (size_t)total, h->pool, st);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&rb.fill, (size_t)(P + 1) * 8, h->pool, st);
+  // fill[0..P], then one word for the record passes' tile queue
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&rb.fill, (size_t)(P + 2) * 8, h->pool, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (rb.keys) cudaFreeAsync(rb.keys, st);
     if (rb.info) cudaFreeAsync(rb.info, st);
+    if (rb.fill) cudaFreeAsync(rb.fill, st);
     return e == cudaErrorMemoryAllocation ? KMA_ENOMEM : cuda_fail(e, "record buckets");
   }
   h->rec_batches.push_back(rb);
   index = h->rec_batches.size() - 1;
-  KMA_CUDA(cudaMemsetAsync(rb.fill, 0, (size_t)(P + 1) * 8, st));
+  KMA_CUDA(cudaMemsetAsync(rb.fill, 0, (size_t)(P + 2) * 8, st));
   return KMA_OK;
 }
 
@@ -537,6 +544,7 @@ int prepare_records(kma_handle* h, u64 n_pos, u64 n_reads, u64 n_bases, cudaStre
 PartRecords records_of(const kma_handle::RecBatch& rb, u64 P) {
   PartRecords r;
   r.keys = rb.keys; r.info = rb.info; r.cap = rb.cap; r.ocap = rb.ocap; r.fill = rb.fill;
+  r.queue = reinterpret_cast<unsigned*>(rb.fill + P + 1);
   r.p_begin = 0; r.p_end = (unsigned)P; r.overflow = 1; r.pad = 0;
   return r;
 }

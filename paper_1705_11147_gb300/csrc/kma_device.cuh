@@ -51,13 +51,22 @@ __device__ __forceinline__ unsigned part_of(u64 h, unsigned P) {
   return __umulhi((unsigned)(h >> 32), P);
 }
 
-// Mask with bit x set for each 6-bit field x taken from the top of g (built in 32-bit halves).
+// Mask with bit x set for each 6-bit field x taken from the top of g (field i at bits
+// 58 - 6i .. 63 - 6i, i < nbits <= kMaxHashBits), built in 32-bit halves. The loop is unrolled
+// so that every field is extracted with constant shifts.
+constexpr unsigned kMaxHashBits = 10;
 __device__ __forceinline__ u64 mask_from_fields(u64 g, unsigned nbits) {
+  const unsigned gh = (unsigned)(g >> 32), gl = (unsigned)g;
   unsigned lo = 0, hi = 0;
-  for (unsigned i = 0; i < nbits; ++i) {
-    const unsigned x = (unsigned)(g >> (58 - 6 * i)) & 63u;
-    const unsigned bit = 1u << (x & 31u);
-    if (x & 32u) hi |= bit; else lo |= bit;
+#pragma unroll
+  for (int i = 0; i < (int)kMaxHashBits; ++i) {
+    if (i < (int)nbits) {
+      const int off = 58 - 6 * i;
+      const unsigned x = off >= 32 ? (gh >> (off - 32)) & 63u
+                                   : (off + 6 <= 32 ? (gl >> off) & 63u : __funnelshift_r(gl, gh, off) & 63u);
+      const unsigned bit = 1u << (x & 31u);
+      if (x & 32u) hi |= bit; else lo |= bit;
+    }
   }
   return ((u64)hi << 32) | lo;
 }
@@ -147,17 +156,20 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Test for the phase; while it is incomplete the thread may be suspended, and it resumes when
+// the phase completes or after at most kWaitHintNs nanoseconds. A waiting warp therefore
+// sleeps instead of spinning (no issue slots spent on polling).
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned phase) {
   unsigned done;
   asm volatile("{\n\t.reg .pred p;\n\t"
-               "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                "selp.u32 %0, 1, 0, p;\n\t}"
-               : "=r"(done) : "r"(bar), "r"(phase) : "memory");
+               : "=r"(done) : "r"(bar), "r"(phase), "n"(kWaitHintNs) : "memory");
   return done != 0;
 }
 
 // Bounded wait for the mbarrier phase: returns false (and the caller raises a status flag)
-// if the copies have not completed after `limit` polls.
+// if the copies have not completed after `limit` polls (at most limit * kWaitHintNs ns).
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned phase, unsigned limit) {
   for (unsigned it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, phase)) return true;
@@ -165,10 +177,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned phase, 
 }
 
 // After a wait that gave up: before the CTA may exit, the bulk copies already issued into its
-// shared memory must land. Waits up to 64 times the first limit (still bounded; copies that
+// shared memory must land. Waits up to 8 times the first limit (still bounded; copies that
 // have not landed by then are reported by the flag the caller already raised).
 __device__ __forceinline__ bool mbar_drain(unsigned bar, unsigned phase, unsigned limit) {
-  for (unsigned r = 0; r < 64; ++r)
+  for (unsigned r = 0; r < 8; ++r)
     if (mbar_wait_bounded(bar, phase, limit)) return true;
   return false;
 }

@@ -25,6 +25,13 @@ constexpr uint64_t kEmpty = ~0ull;          // both key words of an empty slot
 constexpr uint32_t kMaxProbe = 1u << 14;    // probe limit before reporting a full table
 constexpr int kMaxBatch = 64;
 
+// Bounded device waits (bulk-copy staging): polls of an mbarrier before giving up, each poll
+// suspending the thread for at most kWaitHintNs (about 1.3 s in all), and the short limit of
+// the fault-injection test.
+constexpr unsigned kWaitHintNs = 10000;
+constexpr unsigned kWaitPolls = 1u << 17;
+constexpr unsigned kWaitPollsInjected = 1u << 6;
+
 // Status flags raised on the device.
 constexpr uint32_t kFlagFull = 1u;
 constexpr uint32_t kFlagOverflow = 2u;
@@ -190,12 +197,15 @@ struct PartWindows {
 // records without leaving its bucket (or the overflow area). fill[p]
 // counts the records that were assigned to bucket p (those beyond cap went to the overflow
 // area); fill[P] counts the overflow records.
+// The record passes hand out their tiles (32 * rpt records, in bucket order) from a queue:
+// `queue` counts the chunks of tiles taken so far and is zeroed before every launch.
 struct PartRecords {
   void* keys;                   // unsigned long long[] (k <= 32) or ulonglong2[]
   unsigned char* info;
   unsigned long long cap;       // records per bucket
   unsigned long long ocap;      // overflow records
   unsigned long long* fill;     // [P + 1]
+  unsigned* queue;              // record passes: chunks of tiles handed out so far
   // record passes: the buckets of partitions [p_begin, p_end), then the overflow area if
   // `overflow` (the whole batch: 0, P, 1); the scatter ignores these
   unsigned int p_begin, p_end;

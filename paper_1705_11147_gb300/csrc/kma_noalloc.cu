@@ -115,7 +115,7 @@ extern "C" int kmer_analysis_count_small_noalloc(const kma_params* params, const
     PackBatch pb;
     std::memset(&pb, 0, offsetof(PackBatch, d) + sizeof(PackDesc));
     pb.n = 1;
-    pb.wait_limit = 1u << 22;
+    pb.wait_limit = kWaitPolls;
     PackDesc& pd = pb.d[0];
     pd.seq = reinterpret_cast<const unsigned char*>(seq);
     pd.qual = reinterpret_cast<const unsigned char*>(qual);

@@ -15,6 +15,7 @@
 
 namespace kma {
 
+
 __device__ __forceinline__ unsigned char info_of(const Window& w) {
   return (unsigned char)(w.lb | ((unsigned)w.lu << 2) | (w.rb << 3) | ((unsigned)w.ru << 5));
 }
@@ -35,54 +36,65 @@ constexpr int kPartThreads = 256;
 //  1. extract the windows (one set of word loads per thread, then the forward k-mer and its
 //     reverse complement are rolled one base at a time), stage key + info in shared memory,
 //     rank each window inside its partition for this tile (shared-memory atomics);
-//  2. exclusive scan of the per-partition counts (the tile's records sorted by partition) and
-//     one global reservation per partition present (bucket part, overflow part);
+//  2. thread t owns a contiguous chunk of partitions: it reserves each present partition's
+//     run in the bucket (one global atomic, bucket first, the rest in the overflow area) and,
+//     while those atomics are in flight, takes part in the exclusive scan of the counts that
+//     sorts the tile's records by partition;
 //  3. permute the staged records into partition order and write them out: consecutive
 //     threads write consecutive records of the same bucket, so the stores coalesce.
+// A CTA of 512 threads with its 4096-window tile leaves room for two CTAs per SM (with up to
+// about a thousand partitions), so one CTA's block barriers and reservation round trips
+// overlap the other's extraction and stores.
 
 constexpr int kScatterThreads = 1024;
 constexpr int kScatterWpt = 8;
-constexpr int kScatterTile = kScatterThreads * kScatterWpt;  // 8192 (ranks < 2^13, slots < 2^16)
+constexpr int kScatterTile = kScatterThreads * kScatterWpt;  // 4096: ranks and slots < 2^12
+constexpr int kScatterMaxChunk = 4;                          // partitions per thread (4096 / 512)
 
 __host__ __device__ constexpr size_t scatter_smem(unsigned P, int kw) {
   return (size_t)kScatterTile * (kw * 8) +   // staged keys
-         (size_t)kScatterTile +              // staged info
-         (size_t)kScatterTile * 4 +          // sorted order: slot | partition << 16
-         (size_t)P * (4 + 4 + 4 + 8 + 8) +   // cnt, off, n1, gbase, obase
-         512;                                // warp sums, tile total, alignment
+         (size_t)kScatterTile * 4 +          // sorted order: slot | partition << 12
+         (size_t)P * 20 +                    // cnt, off, gbase, n1, obase (32-bit each)
+         (size_t)32 * 4 +                    // warp sums
+         (size_t)kScatterTile;               // staged info
 }
 
 static_assert(scatter_smem(kMaxPartitions, 1) <= 227 * 1024 && scatter_smem(kMaxPartitionsWide, 2) <= 227 * 1024,
               "the scatter's shared memory must fit one CTA for every allowed partition count");
+static_assert(kMaxPartitions <= kScatterThreads * kScatterMaxChunk,
+              "partition numbers must fit the sorted order's 12 bits and the threads' chunks");
 
 template <int KW>
-__global__ void __launch_bounds__(kScatterThreads) part_scatter_kernel(const __grid_constant__ PartGeom G,
-                                                                       const __grid_constant__ PartWindows W,
-                                                                       const __grid_constant__ PartRecords R) {
+__global__ void __launch_bounds__(kScatterThreads, 1) part_scatter_kernel(const __grid_constant__ PartGeom G,
+                                                                          const __grid_constant__ PartWindows W,
+                                                                          const __grid_constant__ PartRecords R) {
   constexpr int kWarps = kScatterThreads / 32;
   extern __shared__ __align__(16) unsigned char s_raw[];
   const unsigned P = G.P;
-  u64* s_keys = reinterpret_cast<u64*>(s_raw);                                   // [tile * KW]
-  u64* s_gbase = s_keys + (size_t)kScatterTile * KW;                             // [P]
-  u64* s_obase = s_gbase + P;                                                    // [P]
-  unsigned* s_order = reinterpret_cast<unsigned*>(s_obase + P);                  // [tile]
-  unsigned* s_cnt = s_order + kScatterTile;                                      // [P]
-  unsigned* s_off = s_cnt + P;                                                   // [P]
-  unsigned* s_n1 = s_off + P;                                                    // [P]
-  unsigned* s_wsum = s_n1 + P;                                                   // [kWarps + 1]
-  unsigned char* s_info = reinterpret_cast<unsigned char*>(s_wsum + 64);         // [tile]
-  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const u64 n_tiles = (W.q1 - W.q0 + kScatterTile - 1) / kScatterTile;
+  u64* s_keys = reinterpret_cast<u64*>(s_raw);                              // [tile * KW]
+  unsigned* s_order = reinterpret_cast<unsigned*>(s_keys + kScatterTile * KW);  // [tile]
+  unsigned* s_cnt = s_order + kScatterTile;                                 // [P] records in this tile
+  unsigned* s_off = s_cnt + P;                                              // [P] first sorted position
+  unsigned* s_gbase = s_off + P;                                            // [P] run start in the bucket
+  unsigned* s_n1 = s_gbase + P;                                             // [P] records of the run in the bucket
+  unsigned* s_obase = s_n1 + P;                                             // [P] rest: overflow area position
+  unsigned* s_wsum = s_obase + P;                                           // [32]
+  unsigned char* s_info = reinterpret_cast<unsigned char*>(s_wsum + 32);    // [tile]
+  const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned n_tiles = (unsigned)((W.q1 - W.q0 + kScatterTile - 1) / kScatterTile);
   const u64 pol = policy_evict_first();
+  const unsigned per = (P + kScatterThreads - 1) / kScatterThreads;  // partitions per thread (<= 8)
+  const unsigned p0 = min(P, tid * per), p1 = min(P, p0 + per);
+  const u64 cap = R.cap, ocap = R.ocap;
   unsigned acc_valid = 0;
-  for (unsigned p = threadIdx.x; p < P; p += blockDim.x) s_cnt[p] = 0;
+  for (unsigned p = tid; p < P; p += kScatterThreads) s_cnt[p] = 0;
   __syncthreads();
-  for (u64 t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+  for (unsigned t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     // 1: windows -> staged records, rank inside the partition
     unsigned pr[kScatterWpt];  // partition << 13 | rank, or ~0u
 #pragma unroll
     for (int j = 0; j < kScatterWpt; ++j) pr[j] = 0xFFFFFFFFu;
-    const u64 q = W.q0 + t * kScatterTile + (u64)threadIdx.x * kScatterWpt;
+    const u64 q = W.q0 + (u64)t * kScatterTile + (u64)tid * kScatterWpt;
     if (q < W.q1) {  // q1 - q0 is a multiple of 64: all kScatterWpt starts are inside
       RollingWindows rw;
       rw.init(W, G.k, q);
@@ -93,11 +105,11 @@ __global__ void __launch_bounds__(kScatterThreads) part_scatter_kernel(const __g
           const u64 h = key_hash(w.lo, w.hi);
           if (G.n_parts <= 1 || owner_of(h, G.n_parts) == G.part) {
             ++acc_valid;
-            const unsigned slot = j * kScatterThreads + threadIdx.x;
+            const unsigned slot = j * kScatterThreads + tid;
             const unsigned p = part_of(h, P);
             pr[j] = (p << 13) | atomicAdd(&s_cnt[p], 1u);
-            s_keys[(size_t)slot * KW] = w.lo;
-            if (KW == 2) s_keys[(size_t)slot * KW + 1] = w.hi;
+            if (KW == 1) s_keys[slot] = w.lo;
+            else reinterpret_cast<ulonglong2*>(s_keys)[slot] = make_ulonglong2(w.lo, w.hi);
             s_info[slot] = info_of(w);
           }
         }
@@ -105,11 +117,20 @@ __global__ void __launch_bounds__(kScatterThreads) part_scatter_kernel(const __g
       }
     }
     __syncthreads();
-    // 2a: exclusive scan of the counts (each thread a contiguous chunk of partitions)
-    const unsigned per = (P + kScatterThreads - 1) / kScatterThreads;
-    const unsigned p0 = threadIdx.x * per, p1 = min(P, p0 + per);
+    // 2: reservations of this thread's partitions (in flight during the scan), then the
+    // exclusive scan of the counts
+    unsigned long long res[kScatterMaxChunk];
     unsigned local = 0;
-    for (unsigned p = p0; p < p1; ++p) local += s_cnt[p];
+#pragma unroll
+    for (unsigned x = 0; x < kScatterMaxChunk; ++x) {
+      const unsigned p = p0 + x;
+      res[x] = 0;
+      if (p < p1) {
+        const unsigned c = s_cnt[p];
+        local += c;
+        if (c) res[x] = atomicAdd(&R.fill[p], (u64)c);
+      }
+    }
     unsigned incl = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -118,31 +139,31 @@ __global__ void __launch_bounds__(kScatterThreads) part_scatter_kernel(const __g
     }
     if (lane == 31) s_wsum[warp] = incl;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned run = 0;
-      for (int x = 0; x < kWarps; ++x) {
-        const unsigned v = s_wsum[x];
-        s_wsum[x] = run;
-        run += v;
-      }
-      s_wsum[kWarps] = run;  // records in this tile
+    // prefix of the warp totals (every warp scans the 16 sums itself)
+    unsigned ws = s_wsum[lane], wincl = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, wincl, o);
+      if (lane >= (unsigned)o) wincl += v;
     }
-    __syncthreads();
-    unsigned run = s_wsum[warp] + incl - local;
-    for (unsigned p = p0; p < p1; ++p) {
-      s_off[p] = run;
-      run += s_cnt[p];
-    }
-    // 2b: reserve each partition's run: bucket first, the rest in the overflow area
-    for (unsigned p = threadIdx.x; p < P; p += blockDim.x) {
-      const unsigned c = s_cnt[p];
-      if (c) {
-        const u64 b = atomicAdd(&R.fill[p], (u64)c);
-        const u64 room = b < R.cap ? R.cap - b : 0;
-        const unsigned n1 = (unsigned)(room < c ? room : c);
-        s_gbase[p] = (u64)p * R.cap + (b < R.cap ? b : 0);
-        s_n1[p] = n1;
-        s_obase[p] = n1 < c ? atomicAdd(&R.fill[P], (u64)(c - n1)) : 0;
+    const unsigned total = __shfl_sync(0xffffffffu, wincl, kWarps - 1);  // records in this tile
+    unsigned run = __shfl_sync(0xffffffffu, wincl - ws, warp) + incl - local;
+#pragma unroll
+    for (unsigned x = 0; x < kScatterMaxChunk; ++x) {
+      const unsigned p = p0 + x;
+      if (p < p1) {
+        const unsigned c = s_cnt[p];
+        s_off[p] = run;
+        run += c;
+        if (c) {
+          const u64 b = res[x];
+          const u64 room = b < cap ? cap - b : 0;
+          const unsigned n1 = (unsigned)(room < c ? room : c);
+          s_gbase[p] = (unsigned)(b < cap ? b : 0);
+          s_n1[p] = n1;
+          s_obase[p] = n1 < c ? (unsigned)min(atomicAdd(&R.fill[P], (u64)(c - n1)), ocap) : 0u;
+        }
+        s_cnt[p] = 0;  // for the next tile
       }
     }
     __syncthreads();
@@ -151,32 +172,29 @@ __global__ void __launch_bounds__(kScatterThreads) part_scatter_kernel(const __g
     for (int j = 0; j < kScatterWpt; ++j) {
       if (pr[j] == 0xFFFFFFFFu) continue;
       const unsigned p = pr[j] >> 13, r = pr[j] & 8191u;
-      s_order[s_off[p] + r] = (j * kScatterThreads + threadIdx.x) | (p << 16);
+      s_order[s_off[p] + r] = (p << 13) | (j * kScatterThreads + tid);
     }
-    for (unsigned p = threadIdx.x; p < P; p += blockDim.x) s_cnt[p] = 0;  // for the next tile
     __syncthreads();
     // 3b: write out in sorted order (coalesced runs per bucket)
-    const unsigned total = s_wsum[kWarps];
-    for (unsigned i = threadIdx.x; i < total; i += blockDim.x) {
+    for (unsigned i = tid; i < total; i += kScatterThreads) {
       const unsigned e = s_order[i];
-      const unsigned slot = e & 0xFFFFu, p = e >> 16;
-      const unsigned r = i - s_off[p];
+      const unsigned slot = e & 8191u, p = e >> 13;
+      const unsigned r = i - s_off[p], n1 = s_n1[p];
       u64 gi;
-      if (r < s_n1[p]) {
-        gi = s_gbase[p] + r;
+      if (r < n1) {
+        gi = (u64)p * cap + s_gbase[p] + r;
       } else {
-        const u64 o = s_obase[p] + (r - s_n1[p]);
-        if (o >= R.ocap) {  // overflow area full: reported, never dropped silently
+        const u64 o = (u64)s_obase[p] + (r - n1);
+        if (o >= ocap) {  // overflow area full: reported, never dropped silently
           atomicOr(&G.status->flags, kFlagFull);
           continue;
         }
-        gi = (u64)P * R.cap + o;
+        gi = (u64)P * cap + o;
       }
       if (KW == 1) {
         st_stream(reinterpret_cast<u64*>(R.keys) + gi, s_keys[slot], pol);
       } else {
-        st_stream(reinterpret_cast<ulonglong2*>(R.keys) + gi,
-                  make_ulonglong2(s_keys[(size_t)slot * 2], s_keys[(size_t)slot * 2 + 1]), pol);
+        st_stream(reinterpret_cast<ulonglong2*>(R.keys) + gi, reinterpret_cast<const ulonglong2*>(s_keys)[slot], pol);
       }
       st_stream(R.info + gi, s_info[slot], pol);
     }
@@ -211,45 +229,72 @@ static_assert(sizeof(WarpStage<1, 2>) % 16 == 0 && sizeof(WarpStage<2, 2>) % 16 
                   sizeof(WarpStage<1, 4>) % 16 == 0 && sizeof(WarpStage<2, 4>) % 16 == 0,
               "every warp's staging buffers must start on a 16-byte boundary");
 
-// Record range [base, end) of tile t, clipped to one tile; false if the tile is empty. The
-// launch numbers its tiles from 0: first the nb tiles of the buckets of partitions
-// [p_begin, p_end), then the tiles of the overflow area (if the launch covers it).
+// Records of launch tile t: the first one (base) and their number, 0 if the tile is empty.
+// The launch numbers its tiles from 0: first the nb tiles of the buckets of partitions
+// [p_begin, p_end), tpb per bucket, then the tiles of the overflow area (if the launch covers
+// it). Tile numbers, bucket numbers and record counts within a bucket fit 32 bits (the host
+// checks each record batch). cb / cf: the bucket whose record count was loaded last.
 template <int TILE>
-__device__ __forceinline__ bool rec_tile(const PartGeom& G, const PartRecords& R, u64 tpb, u64 nb, u64 t,
-                                         u64& base, u64& end) {
-  u64 f, lo, b0;
+__device__ __forceinline__ unsigned rec_tile(const PartGeom& G, const PartRecords& R, unsigned tpb, unsigned nb,
+                                             unsigned t, u64& base, unsigned& cb, unsigned& cf) {
+  unsigned f, lo;
+  u64 b0;
   if (t < nb) {
-    t += (u64)R.p_begin * tpb;
-    const u64 b = ((t | tpb) >> 32) ? t / tpb : (u64)((unsigned)t / (unsigned)tpb);
-    f = R.fill[b] < R.cap ? R.fill[b] : R.cap;
-    lo = (t - b * tpb) * TILE;
-    b0 = b * R.cap;
+    const unsigned q = t / tpb;
+    const unsigned b = R.p_begin + q;
+    if (b != cb) {
+      const u64 x = R.fill[b];
+      cb = b;
+      cf = (unsigned)(x < R.cap ? x : R.cap);
+    }
+    f = cf;
+    lo = (t - q * tpb) * TILE;
+    b0 = (u64)b * R.cap;
   } else {
-    f = R.fill[G.P] < R.ocap ? R.fill[G.P] : R.ocap;
+    const u64 x = R.fill[G.P];
+    f = (unsigned)(x < R.ocap ? x : R.ocap);
     lo = (t - nb) * TILE;
     b0 = (u64)G.P * R.cap;
   }
-  if (lo >= f) return false;
+  if (lo >= f) return 0;
   base = b0 + lo;
-  end = b0 + (f - lo < (u64)TILE ? f : lo + TILE);
-  return true;
+  return f - lo < (unsigned)TILE ? f - lo : (unsigned)TILE;
 }
 
-// First non-empty tile at or after t in steps of `step` (n_tiles if none).
+// Tiles are handed out in launch order from a global queue, kQueueChunk consecutive tiles at a
+// time, so every warp works at the front of the partition sequence: the warps never spread
+// over more partitions than the front touches, and those partitions' sub-filters and
+// sub-tables stay in L2. (Tiles assigned to warps in a fixed pattern let fast and slow warps
+// drift apart over the partitions, and their structures evicted one another from L2.)
+// Lane 0 holds the warp's current chunk (tiles up to c_end) and the next chunk, grabbed one
+// ahead so that its queue round trip is hidden.
+constexpr unsigned kQueueChunk = 8;
+
+// Lane 0: the next non-empty tile from t on (its first record in base, t moved past it),
+// moving through the warp's chunks; returns its record count, 0 when no tile is left.
 template <int TILE>
-__device__ __forceinline__ u64 rec_next(const PartGeom& G, const PartRecords& R, u64 tpb, u64 nb, u64 n_tiles,
-                                        u64 t, u64 step, u64& base, u64& end) {
-  base = end = 0;
-  while (t < n_tiles && !rec_tile<TILE>(G, R, tpb, nb, t, base, end)) t += step;
-  return t;
+__device__ __forceinline__ unsigned rec_next(const PartGeom& G, const PartRecords& R, unsigned tpb, unsigned nb,
+                                             unsigned n_tiles, unsigned& t, unsigned& c_end, unsigned& c_next,
+                                             u64& base, unsigned& cb, unsigned& cf) {
+  while (true) {
+    if (t >= c_end) {  // chunk done: take the one grabbed ahead, grab the following one
+      t = c_next * kQueueChunk;
+      c_end = t + kQueueChunk;
+      c_next = atomicAdd(R.queue, 1u);
+    }
+    if (t >= n_tiles) return 0;
+    const unsigned n = rec_tile<TILE>(G, R, tpb, nb, t, base, cb, cf);
+    ++t;
+    if (n) return n;
+  }
 }
 
-// Lane 0: stage the records [base, end) into buffer `buf` (sizes rounded up to 16 records,
+// Lane 0: stage the n records from `base` into buffer `buf` (sizes rounded up to 16 records,
 // which stays inside the bucket because cap and ocap are multiples of 16).
 template <int KW, int RPT>
-__device__ __forceinline__ void rec_issue(WarpStage<KW, RPT>& S, const PartRecords& R, int buf, u64 base, u64 end,
+__device__ __forceinline__ void rec_issue(WarpStage<KW, RPT>& S, const PartRecords& R, int buf, u64 base, unsigned n,
                                           u64 pol) {
-  const unsigned n16 = (unsigned)((end - base + 15) & ~15ull);
+  const unsigned n16 = (n + 15u) & ~15u;
   const unsigned kb = n16 * 8u * KW;
   const unsigned bar = smem_u32(&S.bar[buf]);
   fence_proxy_async_smem();
@@ -261,56 +306,57 @@ __device__ __forceinline__ void rec_issue(WarpStage<KW, RPT>& S, const PartRecor
 __device__ __forceinline__ u64 shfl0(u64 v) { return __shfl_sync(0xffffffffu, v, 0); }
 
 template <int KW, int RPT, unsigned MODE, bool GROUP>
-__global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount ? 6 : 4) : 2) part_pass_kernel(const __grid_constant__ PartGeom G,
+__global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount ? 5 : 4) : 2) part_pass_kernel(const __grid_constant__ PartGeom G,
                                                                  const __grid_constant__ PartRecords R) {
   constexpr int kTile = WarpStage<KW, RPT>::kTile;
   constexpr int kWarps = kPartThreads / 32;
   __shared__ __align__(128) WarpStage<KW, RPT> stage[kWarps];
   const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpStage<KW, RPT>& S = stage[warp];
-  const u64 step = (u64)gridDim.x * kWarps;
-  const u64 tpb = (R.cap + kTile - 1) / kTile;  // tiles per bucket
-  const u64 ofill = R.fill[G.P] < R.ocap ? R.fill[G.P] : R.ocap;
-  const u64 nb = (u64)(R.p_end - R.p_begin) * tpb;  // bucket tiles of this launch
-  const u64 n_tiles = nb + (R.overflow ? (ofill + kTile - 1) / kTile : 0);
+  const unsigned tpb = (unsigned)((R.cap + kTile - 1) / kTile);  // tiles per bucket
+  const unsigned ofill = (unsigned)(R.fill[G.P] < R.ocap ? R.fill[G.P] : R.ocap);
+  const unsigned nb = (R.p_end - R.p_begin) * tpb;  // bucket tiles of this launch
+  const unsigned n_tiles = nb + (R.overflow ? (ofill + kTile - 1) / kTile : 0u);
   const u64 pol = policy_evict_first();
-  u64 acc_ins = 0, acc_first = 0;
+  unsigned acc_ins = 0, acc_first = 0;  // per warp: below 2^32
   unsigned phases = 0;  // bit b: parity to wait for on buffer b (same in every lane)
 
-  u64 t, base, end;
+  // lane 0's walk over the queue's chunks
+  unsigned t = 0, cb = ~0u, cf = 0, c_end = 0, c_next = 0;
+  u64 base = 0;
+  unsigned n = 0;
   if (lane == 0) {
     mbar_init(smem_u32(&S.bar[0]), 1);
     mbar_init(smem_u32(&S.bar[1]), 1);
-    t = rec_next<kTile>(G, R, tpb, nb, n_tiles, (u64)blockIdx.x * kWarps + warp, step, base, end);
-    if (t < n_tiles) rec_issue(S, R, 0, base, end, pol);
+    c_next = atomicAdd(R.queue, 1u);
+    n = rec_next<kTile>(G, R, tpb, nb, n_tiles, t, c_end, c_next, base, cb, cf);
+    if (n) rec_issue(S, R, 0, base, n, pol);
   }
   __syncwarp();  // barriers initialised before any lane polls them
-  t = shfl0(t);
+  n = __shfl_sync(0xffffffffu, n, 0);
   base = shfl0(base);
-  end = shfl0(end);
   int buf = 0;
-  while (t < n_tiles) {
-    // prefetch the warp's next non-empty tile into the other buffer, then wait for this one
-    u64 tn, nbase, ne;
+  while (n) {
+    // stage the warp's next non-empty tile into the other buffer, then wait for this one
+    u64 nbase = 0;
+    unsigned nn = 0;
     if (lane == 0) {
-      tn = rec_next<kTile>(G, R, tpb, nb, n_tiles, t + step, step, nbase, ne);
-      if (tn < n_tiles) rec_issue(S, R, buf ^ 1, nbase, ne, pol);
+      nn = rec_next<kTile>(G, R, tpb, nb, n_tiles, t, c_end, c_next, nbase, cb, cf);
+      if (nn) rec_issue(S, R, buf ^ 1, nbase, nn, pol);
     }
-    tn = shfl0(tn);
+    nn = __shfl_sync(0xffffffffu, nn, 0);
     nbase = shfl0(nbase);
-    ne = shfl0(ne);
     const unsigned bar = smem_u32(&S.bar[buf]);
     const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, (phases >> buf) & 1u, G.wait_limit));
     if (!ok) {  // give up: report, let the copies in flight land (bounded), stop the warp
       if (lane == 0) {
         atomicOr(&G.status->flags, kFlagTimeout);
         mbar_drain(bar, (phases >> buf) & 1u, G.wait_limit);
-        if (tn < n_tiles) mbar_drain(smem_u32(&S.bar[buf ^ 1]), (phases >> (buf ^ 1)) & 1u, G.wait_limit);
+        if (nn) mbar_drain(smem_u32(&S.bar[buf ^ 1]), (phases >> (buf ^ 1)) & 1u, G.wait_limit);
       }
       return;
     }
     phases ^= 1u << buf;
-    const unsigned n = (unsigned)(end - base);
     const u64* sk = S.keys[buf];
     const unsigned char* si = S.info[buf];
 
@@ -479,14 +525,13 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
       }
     }
     __syncwarp();  // buffer `buf` (and the list) are free for the next copy
-    t = tn;
+    n = nn;
     base = nbase;
-    end = ne;
     buf ^= 1;
   }
   if (lane == 0) {
-    if (acc_ins) atomicAdd(&G.status->table_keys, acc_ins);
-    if (acc_first) atomicAdd(&G.status->first_sightings, acc_first);
+    if (acc_ins) atomicAdd(&G.status->table_keys, (u64)acc_ins);
+    if (acc_first) atomicAdd(&G.status->first_sightings, (u64)acc_first);
   }
 }
 
@@ -557,6 +602,8 @@ static cudaError_t launch_pass_rt(const PartGeom& g, const PartRecords& r, cudaS
   const void* fn = (const void*)part_pass_kernel<KW, RPT, MODE, GROUP>;
   u64 grid = grid_for(fn, kPartThreads, 0, num_sms);
   if (grid > tiles) grid = tiles;
+  cudaError_t e = cudaMemsetAsync(r.queue, 0, sizeof(unsigned), stream);  // the launch's tile queue
+  if (e != cudaSuccess) return e;
   part_pass_kernel<KW, RPT, MODE, GROUP><<<(unsigned)grid, kPartThreads, 0, stream>>>(g, r);
   return cudaGetLastError();
 }
