@@ -682,6 +682,67 @@ def run_served(args, ws, rank, local):
             "latency": {"jobs": n_lat, "rate_per_s": 4.0, **lat}, "generation_s": round(t_gen, 1)}
 
 
+# ------------------------------------------------------------------ heavy hitters (satellite)
+
+def run_satellite(args, ws, rank, local):
+    """Heavy hitters (Section 5.1): a read set with a tandem satellite in 30 % of its reads.
+    The cardinality pass (HyperLogLog + Misra-Gries summaries) runs first, as the paper's
+    sizing pass does; its heavy-hitter recommendation chooses the counting mode (warp-level
+    grouping of equal keys). Both modes are timed over the same steps (count + finalize)."""
+    import torch
+    from paper_1705_11147_gb300 import KmerAnalysis, estimate_distinct
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rs = synth.satellite_workload(args.scale)
+    seq = torch.from_numpy(rs.seq).to(dev)
+    qual = torch.from_numpy(rs.qual).to(dev)
+    offs = torch.from_numpy(rs.offsets.astype(np.int64)).to(dev)
+    k = rs.meta["params"]["k"]
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    est = estimate_distinct(seq, qual, offs, k=k, stream=stream)
+    t_est = time.perf_counter() - t0
+
+    def timed(heavy):
+        with KmerAnalysis(make_handle_params(rs, heavy_hitters=heavy), stream=stream) as ka:
+            def step():
+                ka.reset()
+                ka.count(seq, qual, offs)
+                return ka.finalize()
+            for _ in range(args.warmup):
+                step()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            ev0.record(stream)
+            for _ in range(args.steps):
+                info = step()
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            return ev0.elapsed_time(ev1) / args.steps, info
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_rec, info = timed(bool(est.heavy_hitters))
+    ms_other, info2 = timed(not est.heavy_hitters)
+    clk = clocks.stop()
+    assert int(info.n) == int(info2.n) and int(info.valid_windows) == int(info2.valid_windows)
+    W = int(info.valid_windows)
+    return {"metric": METRIC, "value": round(W / (ms_rec * 1e-3) / 1e9, 3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_rec, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "satellite_50m", "scale": args.scale, "bases": rs.n_bases,
+                       "reads": rs.n_reads, "valid_windows": W, "k": k, "kmers_out": int(info.n),
+                       "step": "reset -> count -> finalize (device-resident reads)"},
+            "sizing_pass": {"ms": round(t_est * 1e3, 2), "heavy_hitters": bool(est.heavy_hitters),
+                            "sampled_windows": est.sampled_windows, "heavy_threshold": est.heavy_threshold,
+                            "top_counts": [int(x) for x in est.summary_counts[:8]]},
+            "grouping": {"recommended": bool(est.heavy_hitters), "ms_recommended": round(ms_rec, 3),
+                         "ms_other": round(ms_other, 3), "speedup": round(ms_other / ms_rec, 3)},
+            "clocks": clk}
+
+
 # ------------------------------------------------------------------ reference arm
 
 def oracle_sample_reads(rs, budget_s: float, threads: int) -> int:
@@ -738,7 +799,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large_200m",
-                    choices=list(synth.WORKLOADS) + ["batched_64", "served_500"])
+                    choices=list(synth.WORKLOADS) + ["batched_64", "served_500", "satellite_50m"])
     ap.add_argument("--samples", type=int, default=64)
     ap.add_argument("--jobs", type=int, default=500)
     ap.add_argument("--latency-jobs", type=int, default=60)
@@ -768,6 +829,8 @@ def main():
             out = run_batched(args, ws, rank, local)
         elif args.workload == "served_500":
             out = run_served(args, ws, rank, local)
+        elif args.workload == "satellite_50m":
+            out = run_satellite(args, ws, rank, local)
         else:
             out = run_ours(args, ws, rank, local)
     if out is not None and rank == 0:

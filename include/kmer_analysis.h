@@ -348,12 +348,33 @@ int kmer_analysis_copy_contigs(kma_handle* h, char* seq, uint64_t* offsets, int 
 #define KMA_HLL_MIN_PRECISION 4
 #define KMA_HLL_MAX_PRECISION 14
 
+/* Heavy hitters (Section 5.1: frequent k-mers are found in the same pass, so that they can be
+ * accumulated locally). The windows starting at every KMA_MG_SAMPLE-th position of the packed
+ * reads (read r's base j at offsets[r] - offsets[0] + r + j; one separator per read) form a
+ * sampled stream, split by the top 5 bits of the key hash into KMA_MG_BUCKETS sub-streams.
+ * Each is summarised by the Misra-Gries algorithm with KMA_MG_COUNTERS counters (per CTA, then
+ * merged: counts of a key summed, the (m+1)-th largest subtracted): for a sub-stream of n
+ * sampled windows, every key with sampled frequency f > n / (m + 1) is in the summary, with a
+ * count c, f - n / (m + 1) <= c <= f; keys not in it have f <= n / (m + 1). */
+#define KMA_MG_SAMPLE 16
+#define KMA_MG_BUCKETS 32
+#define KMA_MG_COUNTERS 32
+
 typedef struct {
   uint32_t precision;       /* in: p (KMA_HLL_MIN_PRECISION .. KMA_HLL_MAX_PRECISION; 0 = 14) */
-  uint32_t pad;
+  uint32_t heavy_hitters;   /* out: 1 if some k-mer's summary count (a lower bound of its sampled
+                               frequency) reaches heavy_threshold: pass it as kma_params.heavy_hitters */
   double distinct;          /* out: estimated distinct canonical k-mers (of the merged sketch) */
   double rel_std_error;     /* out: 1.04 / sqrt(2^p) */
   uint64_t valid_windows;   /* out: valid windows this call saw (exact; owned keys only) */
+  uint64_t sampled_windows; /* out: windows of the sampled stream (owned keys only) */
+  uint64_t heavy_threshold; /* out: max(1, sampled_windows / 2048) */
+  uint64_t n_summary;       /* out: keys in the merged summaries (<= buckets * counters) */
+  uint64_t summary_capacity;     /* in: rows of the arrays below (0: not wanted) */
+  uint64_t* summary_keys;        /* in: host [capacity][2] or NULL; out: keys, by count descending */
+  uint64_t* summary_counts;      /* in: host [capacity] or NULL; out: their summary counts */
+  uint32_t* summary_bucket;      /* in: host [capacity] or NULL; out: their sub-stream */
+  uint64_t* bucket_windows;      /* in: host [KMA_MG_BUCKETS] or NULL; out: n of each sub-stream */
 } kma_estimate;
 
 /* One estimation pass over reads given like kmer_analysis_count's (host pointers, or device
@@ -362,7 +383,8 @@ typedef struct {
  * the reads need, packs them with the counting path's kernel, runs the sketch kernel and
  * frees everything before it returns; it synchronises `cuda_stream`). `registers`, if not
  * NULL, is a host array of 2^p bytes: on entry a sketch to merge with (all zero = empty), on
- * return the merged sketch; the estimate is that of the merged sketch.
+ * return the merged sketch; the estimate is that of the merged sketch. The heavy-hitter
+ * summaries cover this call's reads only (they are not merged across calls).
  * Errors: KMA_EINVAL (params, precision, offsets), KMA_ENOMEM, KMA_ECUDA. */
 int kmer_analysis_estimate(const kma_params* params, const char* seq, const char* qual,
                            const uint64_t* offsets, uint64_t n_reads, int on_device,

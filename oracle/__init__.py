@@ -55,6 +55,15 @@ def _lib():
         lib.oracle_hll_registers.argtypes = [p, u64, u32, p]
         lib.oracle_hll_estimate.argtypes = [p, u32]
         lib.oracle_hll_estimate.restype = ctypes.c_double
+        lib.oracle_sampled_stream.argtypes = [p, p, p, u64, ctypes.POINTER(_Params), u32]
+        lib.oracle_sampled_stream.restype = p
+        lib.oracle_stream_size.argtypes = [p]
+        lib.oracle_stream_size.restype = u64
+        lib.oracle_stream_fetch.argtypes = [p, p]
+        lib.oracle_stream_free.argtypes = [p]
+        lib.oracle_stream_bucket.argtypes = [p, u64, u32, p]
+        lib.oracle_misra_gries.argtypes = [p, u64, u32, p, p]
+        lib.oracle_misra_gries.restype = u64
         lib.oracle_contigs.argtypes = [p, p, u64, u32, ctypes.c_int]
         lib.oracle_contigs.restype = p
         for fn in ("oracle_contigs_n", "oracle_contigs_bases", "oracle_contigs_cycles"):
@@ -199,6 +208,46 @@ def hll_estimate(registers: np.ndarray, precision: int) -> float:
     r = np.ascontiguousarray(registers, dtype=np.uint8)
     assert r.shape == (1 << precision,)
     return float(_lib().oracle_hll_estimate(r.ctypes.data, precision))
+
+
+def sampled_stream(seq: np.ndarray, qual: np.ndarray, offsets: np.ndarray, k: int, canonical: bool = True,
+                   sample: int = 16, **_) -> np.ndarray:
+    """Keys (uint64[n, 2]) of the valid windows starting at every `sample`-th position of the
+    reads laid out back to back with one separator after each read, in read order (the
+    stream the heavy-hitter summaries of the cardinality pass are defined on)."""
+    seq = np.ascontiguousarray(seq, dtype=np.uint8)
+    qual = np.ascontiguousarray(qual, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    prm = _Params(k, 1, 1, 0, 33, int(bool(canonical)))
+    lib = _lib()
+    h = lib.oracle_sampled_stream(seq.ctypes.data, qual.ctypes.data, offsets.ctypes.data, offsets.shape[0] - 1,
+                                  ctypes.byref(prm), sample)
+    try:
+        n = lib.oracle_stream_size(h)
+        out = np.zeros((n, 2), np.uint64)
+        if n:
+            lib.oracle_stream_fetch(h, out.ctypes.data)
+        return out
+    finally:
+        lib.oracle_stream_free(h)
+
+
+def stream_bucket(keys: np.ndarray, bits: int) -> np.ndarray:
+    """Sub-stream of each key: the top `bits` bits of the sketch hash."""
+    q = np.ascontiguousarray(keys, dtype=np.uint64).reshape(-1, 2)
+    out = np.zeros(q.shape[0], np.uint32)
+    _lib().oracle_stream_bucket(q.ctypes.data, q.shape[0], bits, out.ctypes.data)
+    return out
+
+
+def misra_gries(stream: np.ndarray, m: int):
+    """Misra-Gries summary with m counters of a stream of keys (uint64[n, 2]): (keys, counts)
+    of the keys left with a positive counter."""
+    q = np.ascontiguousarray(stream, dtype=np.uint64).reshape(-1, 2)
+    keys = np.zeros((m, 2), np.uint64)
+    counts = np.zeros(m, np.uint64)
+    n = _lib().oracle_misra_gries(q.ctypes.data, q.shape[0], m, keys.ctypes.data, counts.ctypes.data)
+    return keys[:n], counts[:n]
 
 
 def parse_fastq(text: bytes):

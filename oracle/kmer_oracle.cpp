@@ -454,6 +454,97 @@ void oracle_hll_registers(const uint64_t* keys, uint64_t n, uint32_t p, uint8_t*
 // Flajolet, Fusy, Gandouet, Meunier (2007): E = alpha_m m^2 / sum_j 2^(-M[j]); if E <= 5m/2
 // and V > 0 registers are zero, E = m ln(m / V) (linear counting). With 64-bit hashes the
 // large-range correction of the 32-bit original is not needed.
+// Heavy hitters (Section 5.1: frequent k-mers found in the cardinality pass).
+//
+// The sampled stream: the canonical keys of the valid windows that start at every
+// `sample`-th position of the reads laid out back to back with one separator after each read
+// (read r's base j at offsets[r] - offsets[0] + r + j), in read order.
+struct KeyStream {
+  std::vector<uint64_t> keys;  // (lo, hi) pairs
+};
+
+void* oracle_sampled_stream(const uint8_t* seq, const uint8_t* qual, const uint64_t* offsets, uint64_t n_reads,
+                            const oracle_params* op, uint32_t sample) {
+  (void)qual;
+  KeyStream* out = new KeyStream();
+  const int64_t k = op->k;
+  std::string s;
+  char rc[64];
+  for (uint64_t r = 0; r < n_reads; ++r) {
+    const int64_t L = (int64_t)(offsets[r + 1] - offsets[r]);
+    const uint64_t start = offsets[r] - offsets[0] + r;  // position of the read's first base
+    s.assign((size_t)L, ' ');
+    for (int64_t j = 0; j < L; ++j) s[(size_t)j] = fold(seq[offsets[r] + j]);
+    for (int64_t i = 0; i + k <= L; ++i) {
+      if ((start + (uint64_t)i) % sample != 0) continue;
+      bool ok = true;
+      for (int64_t j = 0; j < k; ++j) ok = ok && is_acgt(s[(size_t)(i + j)]);
+      if (!ok) continue;
+      const char* w = s.data() + i;
+      for (int64_t j = 0; j < k; ++j) rc[j] = complement(w[k - 1 - j]);
+      const bool forward = !op->canonical || std::memcmp(w, rc, (size_t)k) <= 0;
+      const Key key = pack_chars(forward ? w : rc, k);
+      out->keys.push_back(key[0]);
+      out->keys.push_back(key[1]);
+    }
+  }
+  return out;
+}
+
+uint64_t oracle_stream_size(void* h) { return ((KeyStream*)h)->keys.size() / 2; }
+
+void oracle_stream_fetch(void* h, uint64_t* keys) {
+  const KeyStream* st = (KeyStream*)h;
+  std::memcpy(keys, st->keys.data(), st->keys.size() * sizeof(uint64_t));
+}
+
+void oracle_stream_free(void* h) { delete (KeyStream*)h; }
+
+// Sub-stream of a key: the top `bits` bits of the sketch hash (the same hash as the
+// HyperLogLog registers).
+void oracle_stream_bucket(const uint64_t* keys, uint64_t n, uint32_t bits, uint32_t* out) {
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint64_t lo = keys[2 * i], hi = keys[2 * i + 1];
+    const uint64_t h = sketch_fmix64(lo ^ (hi * 0x9e3779b97f4a7c15ull + 0x632be59bd9b4e019ull));
+    out[i] = (uint32_t)(h >> (64 - bits));
+  }
+}
+
+// Misra and Gries (1982), "Finding repeated elements", taken item by item over a stream of
+// keys with m counters: a key that holds a counter increments it; otherwise, if a counter is
+// free (zero), the key takes it with count 1; otherwise every counter is decremented (those
+// reaching zero are freed) and the item is dropped. Returns the number of keys left with a
+// positive count; keys/counts receive them (up to m rows), in counter order.
+uint64_t oracle_misra_gries(const uint64_t* stream, uint64_t n, uint32_t m, uint64_t* keys, uint64_t* counts) {
+  std::vector<Key> held(m);
+  std::vector<uint64_t> c(m, 0);
+  for (uint64_t i = 0; i < n; ++i) {
+    const Key x{stream[2 * i], stream[2 * i + 1]};
+    int64_t at = -1, free_at = -1;
+    for (uint32_t j = 0; j < m; ++j) {
+      if (c[j] > 0 && held[j] == x) at = j;
+      if (c[j] == 0 && free_at < 0) free_at = j;
+    }
+    if (at >= 0) {
+      ++c[(size_t)at];
+    } else if (free_at >= 0) {
+      held[(size_t)free_at] = x;
+      c[(size_t)free_at] = 1;
+    } else {
+      for (uint32_t j = 0; j < m; ++j) --c[j];
+    }
+  }
+  uint64_t out = 0;
+  for (uint32_t j = 0; j < m; ++j)
+    if (c[j] > 0) {
+      keys[2 * out] = held[j][0];
+      keys[2 * out + 1] = held[j][1];
+      counts[out] = c[j];
+      ++out;
+    }
+  return out;
+}
+
 double oracle_hll_estimate(const uint8_t* regs, uint32_t p) {
   const uint64_t m = 1ull << p;
   const double md = (double)m;

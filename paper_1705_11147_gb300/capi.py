@@ -66,11 +66,14 @@ class kma_contigs(ctypes.Structure):
 
 
 class kma_estimate(ctypes.Structure):
-    _fields_ = [("precision", u32), ("pad", u32), ("distinct", dbl), ("rel_std_error", dbl),
-                ("valid_windows", u64)]
+    _fields_ = [("precision", u32), ("heavy_hitters", u32), ("distinct", dbl), ("rel_std_error", dbl),
+                ("valid_windows", u64), ("sampled_windows", u64), ("heavy_threshold", u64),
+                ("n_summary", u64), ("summary_capacity", u64), ("summary_keys", vp),
+                ("summary_counts", vp), ("summary_bucket", vp), ("bucket_windows", vp)]
 
 
 HLL_MIN_PRECISION, HLL_MAX_PRECISION = 4, 14
+MG_SAMPLE, MG_BUCKETS, MG_COUNTERS = 16, 32, 32
 
 
 class kma_reads(ctypes.Structure):

@@ -103,7 +103,7 @@ struct Derived {
 constexpr double kKeyFilterBitsPerKey = 12.0;
 
 constexpr u64 kAutoPartitionAbove = 256ull << 20;  // filter + table bytes
-constexpr u64 kPartitionTarget = 48ull << 20;      // filter + table bytes per partition
+constexpr u64 kPartitionTarget = 64ull << 20;      // filter + table bytes per partition
 
 int check_params(const kma_params* p) {
   if (!p) return KMA_EINVAL;
@@ -212,6 +212,45 @@ int get_pool(int dev, cudaMemPool_t* out) {
   }
   *out = g_pools[dev];
   return KMA_OK;
+}
+
+// Heavy hitters: the CTAs' Misra-Gries summaries of one sub-stream merged into one (mergeable
+// summaries, Agarwal et al. 2012): the counts of each key are summed; if more than m keys
+// remain, the (m+1)-th largest count is subtracted from every count and the keys left at zero
+// or below are dropped. The merged summary keeps the bound of its parts: for a sub-stream of n
+// items, every key with frequency f > n / (m + 1) is present with f - n / (m + 1) <= c <= f.
+struct MgEntry {
+  u64 lo, hi, count;
+  unsigned bucket;
+};
+
+void mg_merge(const std::vector<u64>& lo, const std::vector<u64>& hi, const std::vector<unsigned>& cnt,
+              unsigned grid, std::vector<MgEntry>& out) {
+  out.clear();
+  for (unsigned b = 0; b < kMgBuckets; ++b) {
+    std::vector<MgEntry> e;
+    for (unsigned c = 0; c < grid; ++c)
+      for (unsigned i = 0; i < kMgCounters; ++i) {
+        const u64 o = ((u64)c * kMgBuckets + b) * kMgCounters + i;
+        if (cnt[o]) e.push_back({lo[o], hi[o], cnt[o], b});
+      }
+    std::sort(e.begin(), e.end(), [](const MgEntry& x, const MgEntry& y) {
+      return x.hi != y.hi ? x.hi < y.hi : x.lo < y.lo;
+    });
+    std::vector<MgEntry> sum;  // one entry per key
+    for (const MgEntry& x : e) {
+      if (!sum.empty() && sum.back().lo == x.lo && sum.back().hi == x.hi) sum.back().count += x.count;
+      else sum.push_back(x);
+    }
+    std::sort(sum.begin(), sum.end(), [](const MgEntry& x, const MgEntry& y) { return x.count > y.count; });
+    const u64 delta = sum.size() > kMgCounters ? sum[kMgCounters].count : 0;
+    for (MgEntry& x : sum)
+      if (x.count > delta) {
+        x.count -= delta;
+        out.push_back(x);
+      }
+  }
+  std::stable_sort(out.begin(), out.end(), [](const MgEntry& x, const MgEntry& y) { return x.count > y.count; });
 }
 
 }  // namespace
@@ -1354,31 +1393,71 @@ int kmer_analysis_estimate(const kma_params* params, const char* seq, const char
   std::vector<unsigned> regs32(m, 0);
   if (registers)
     for (u64 j = 0; j < m; ++j) regs32[j] = registers[j];
-  unsigned* d_regs = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync((void**)&d_regs, m * 4, h->pool, h->stream);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    kmer_analysis_destroy(h);
-    return e == cudaErrorMemoryAllocation ? KMA_ENOMEM : cuda_fail(e, "sketch registers");
-  }
+  // device temporaries: sketch registers, the CTAs' heavy-hitter summaries, and (host input)
+  // the reads, copied whole so that they are packed as one batch (the sampled stream is
+  // defined on the positions of one packed batch)
+  const unsigned grid = hll_grid(p, h->num_sms);
+  const u64 mg_n = (u64)grid * kMgBuckets * kMgCounters;
+  std::vector<void*> temps;
   auto finish = [&](int code) {
-    cudaFreeAsync(d_regs, h->stream);
+    for (void* t : temps) cudaFreeAsync(t, h->stream);
     kmer_analysis_destroy(h);
     return code;
   };
+  auto temp = [&](void** ptr, u64 bytes) -> int {
+    cudaError_t e = cudaMallocFromPoolAsync(ptr, std::max<u64>(bytes, 16), h->pool, h->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *ptr = nullptr;
+      return e == cudaErrorMemoryAllocation ? KMA_ENOMEM : cuda_fail(e, "estimate temporaries");
+    }
+    temps.push_back(*ptr);
+    return KMA_OK;
+  };
+  unsigned* d_regs = nullptr;
+  MgOut mg{nullptr, nullptr, nullptr, nullptr};
+  if ((rc = temp((void**)&d_regs, m * 4)) || (rc = temp((void**)&mg.lo, mg_n * 8)) ||
+      (rc = temp((void**)&mg.hi, mg_n * 8)) || (rc = temp((void**)&mg.count, mg_n * 4)) ||
+      (rc = temp((void**)&mg.items, (u64)grid * kMgBuckets * 8)))
+    return finish(rc);
+  cudaError_t e;
   if ((e = cudaMemcpyAsync(d_regs, regs32.data(), m * 4, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
     return finish(cuda_fail(e, "sketch registers in"));
-  if (n_reads && (rc = kmer_analysis_count(h, seq, qual, offsets, n_reads, on_device))) return finish(rc);
+  if (n_reads) {
+    const char *s_in = seq, *q_in = qual;
+    const uint64_t* o_in = offsets;
+    if (!on_device) {
+      const u64 nb = ends[1] - ends[0];
+      void *ds = nullptr, *dq = nullptr, *dof = nullptr;
+      if ((rc = temp(&ds, nb)) || (rc = temp(&dq, nb)) || (rc = temp(&dof, (n_reads + 1) * 8))) return finish(rc);
+      if ((e = cudaMemcpyAsync(ds, seq + ends[0], nb, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(dq, qual + ends[0], nb, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(dof, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+        return finish(cuda_fail(e, "estimate reads in"));
+      // the device copy of the bases starts at offsets[0]
+      s_in = (const char*)ds - ends[0];
+      q_in = (const char*)dq - ends[0];
+      o_in = (const uint64_t*)dof;
+    }
+    if ((rc = kmer_analysis_count(h, s_in, q_in, o_in, n_reads, 1))) return finish(rc);
+  }
   PartWindows w;
   w.codes = h->codes; w.rcodes = h->rcodes; w.inv = h->inv; w.hq = h->hq;
   w.q0 = 0; w.q1 = h->q_used;
   const unsigned n_parts = params->n_parts > 1 ? params->n_parts : 1;
   const unsigned part = params->n_parts > 1 ? params->part : 0;
-  if ((e = launch_hll(w, params->k, params->canonical, n_parts, part, p, d_regs, h->status, h->stream,
-                      h->num_sms)) != cudaSuccess)
+  if ((e = launch_hll(w, params->k, params->canonical, n_parts, part, p, d_regs, h->status, mg, grid,
+                      h->stream)) != cudaSuccess)
     return finish(cuda_fail(e, "hll_kernel"));
-  if ((e = cudaMemcpyAsync(regs32.data(), d_regs, m * 4, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
-    return finish(cuda_fail(e, "sketch registers out"));
+  std::vector<u64> mlo(mg_n), mhi(mg_n), items((u64)grid * kMgBuckets);
+  std::vector<unsigned> mcnt(mg_n);
+  if ((e = cudaMemcpyAsync(regs32.data(), d_regs, m * 4, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(mlo.data(), mg.lo, mg_n * 8, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(mhi.data(), mg.hi, mg_n * 8, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(mcnt.data(), mg.count, mg_n * 4, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(items.data(), mg.items, items.size() * 8, cudaMemcpyDeviceToHost, h->stream)) !=
+          cudaSuccess)
+    return finish(cuda_fail(e, "estimate results out"));
   if ((rc = read_status(h))) return finish(rc);
   if ((rc = flags_to_code(h->host_status->flags))) return finish(rc);
   std::vector<uint8_t> regs8(m);
@@ -1388,6 +1467,26 @@ int kmer_analysis_estimate(const kma_params* params, const char* seq, const char
   est->distinct = hll_estimate(regs8.data(), p);
   est->rel_std_error = 1.04 / std::sqrt((double)m);
   est->valid_windows = h->host_status->valid_windows;
+  // heavy hitters: merge the summaries, report the keys by count
+  std::vector<u64> bucket_n(kMgBuckets, 0);
+  for (unsigned c = 0; c < grid; ++c)
+    for (unsigned b = 0; b < kMgBuckets; ++b) bucket_n[b] += items[(u64)c * kMgBuckets + b];
+  std::vector<MgEntry> merged;
+  mg_merge(mlo, mhi, mcnt, grid, merged);
+  u64 sampled = 0;
+  for (u64 x : bucket_n) sampled += x;
+  est->sampled_windows = sampled;
+  est->heavy_threshold = std::max<u64>(1, sampled / 2048);
+  est->heavy_hitters = !merged.empty() && merged[0].count >= est->heavy_threshold ? 1u : 0u;
+  est->n_summary = merged.size();
+  const u64 rows = std::min<u64>(est->summary_capacity, merged.size());
+  for (u64 i = 0; i < rows; ++i) {
+    if (est->summary_keys) { est->summary_keys[2 * i] = merged[i].lo; est->summary_keys[2 * i + 1] = merged[i].hi; }
+    if (est->summary_counts) est->summary_counts[i] = merged[i].count;
+    if (est->summary_bucket) est->summary_bucket[i] = merged[i].bucket;
+  }
+  if (est->bucket_windows)
+    for (unsigned b = 0; b < kMgBuckets; ++b) est->bucket_windows[b] = bucket_n[b];
   return finish(KMA_OK);
 }
 

@@ -243,9 +243,30 @@ int contig_pass(const unsigned long long* keys, const unsigned char* codes, unsi
                 unsigned long long** offsets_out, unsigned long long* n_contigs, unsigned long long* n_bases,
                 unsigned long long* n_vertices, unsigned long long* n_cycles, unsigned* dev_flags, cudaError_t* err);
 
-// HyperLogLog registers (2^p, 32-bit each) of the windows [w.q0, w.q1) (kma_hll.cu).
+// Heavy-hitter summaries of the cardinality pass (kma_hll.cu): the windows at every
+// 2^kMgSampleShift-th arena position, split by the top kMgBucketBits bits of the key hash into
+// kMgBuckets sub-streams, one Misra-Gries summary of kMgCounters counters per sub-stream and CTA.
+constexpr unsigned kMgSampleShift = 4;
+constexpr unsigned kMgBucketBits = 5;
+constexpr unsigned kMgBuckets = 1u << kMgBucketBits;
+constexpr unsigned kMgCounters = 32;
+
+// Where the CTAs leave their summaries: entry [cta][bucket][counter] (lo, hi, count; count 0
+// = unused), items[cta][bucket] = sampled windows of that bucket the CTA saw. lo == nullptr:
+// no summaries.
+struct MgOut {
+  unsigned long long* lo;
+  unsigned long long* hi;
+  unsigned* count;
+  unsigned long long* items;
+};
+
+// HyperLogLog registers (2^p, 32-bit each) of the windows [w.q0, w.q1), and the heavy-hitter
+// summaries of `grid` CTAs (kma_hll.cu); hll_grid gives the number of resident CTAs.
+unsigned hll_grid(unsigned p, int num_sms);
 cudaError_t launch_hll(const PartWindows& w, unsigned k, unsigned canonical, unsigned n_parts, unsigned part,
-                       unsigned p, unsigned* regs, DevStatus* st, cudaStream_t stream, int num_sms);
+                       unsigned p, unsigned* regs, DevStatus* st, const MgOut& mg, unsigned grid,
+                       cudaStream_t stream);
 
 struct LaunchShape {
   int block_threads;

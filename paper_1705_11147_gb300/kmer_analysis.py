@@ -395,12 +395,22 @@ def count_kmers(seq, qual, offsets, k: int, min_depth: int = 2, min_ext_count: i
 
 @dataclass
 class Estimate:
-    """HyperLogLog estimate of the distinct canonical k-mers of a read set (Section 5.1)."""
+    """The cardinality pass over a read set (Section 5.1): HyperLogLog estimate of the distinct
+    canonical k-mers, and the heavy hitters found by the Misra-Gries summaries of the sampled
+    window stream (every capi.MG_SAMPLE-th position, capi.MG_BUCKETS sub-streams by key hash,
+    capi.MG_COUNTERS counters each)."""
     distinct: float
     rel_std_error: float
     valid_windows: int
     precision: int
     registers: np.ndarray  # uint8[2^precision]; merge sketches by np.maximum
+    heavy_hitters: bool = False        # pass as make_params(heavy_hitters=...)
+    sampled_windows: int = 0
+    heavy_threshold: int = 0
+    summary_keys: np.ndarray = None    # uint64[n, 2], by count descending
+    summary_counts: np.ndarray = None  # uint64[n]
+    summary_bucket: np.ndarray = None  # uint32[n]
+    bucket_windows: np.ndarray = None  # uint64[MG_BUCKETS]: items of each sub-stream
 
 
 def estimate_distinct(seq, qual, offsets, k: int, canonical: bool = True, precision: int = 14,
@@ -418,7 +428,14 @@ def estimate_distinct(seq, qual, offsets, k: int, canonical: bool = True, precis
         np.ascontiguousarray(registers, dtype=np.uint8).copy()
     if regs.shape != (1 << precision,):
         raise ValueError("registers must hold 2^precision bytes")
-    est = capi.kma_estimate(precision=precision)
+    cap = capi.MG_BUCKETS * capi.MG_COUNTERS
+    s_keys = np.zeros((cap, 2), np.uint64)
+    s_counts = np.zeros(cap, np.uint64)
+    s_bucket = np.zeros(cap, np.uint32)
+    b_windows = np.zeros(capi.MG_BUCKETS, np.uint64)
+    est = capi.kma_estimate(precision=precision, summary_capacity=cap, summary_keys=s_keys.ctypes.data,
+                            summary_counts=s_counts.ctypes.data, summary_bucket=s_bucket.ctypes.data,
+                            bucket_windows=b_windows.ctypes.data)
     if on_dev:
         args = (seq.data_ptr(), qual.data_ptr(), offsets.data_ptr(), n_reads, 1)
     else:
@@ -428,8 +445,10 @@ def estimate_distinct(seq, qual, offsets, k: int, canonical: bool = True, precis
         args = (seq.ctypes.data, qual.ctypes.data, offsets.ctypes.data, n_reads, 0)
     check(lib.kmer_analysis_estimate(ctypes.byref(p), *args, _stream_handle(stream), ctypes.byref(est),
                                      regs.ctypes.data), "estimate")
+    n = int(est.n_summary)
     return Estimate(float(est.distinct), float(est.rel_std_error), int(est.valid_windows),
-                    int(est.precision), regs)
+                    int(est.precision), regs, bool(est.heavy_hitters), int(est.sampled_windows),
+                    int(est.heavy_threshold), s_keys[:n], s_counts[:n], s_bucket[:n], b_windows)
 
 
 def hll_estimate(registers: np.ndarray, precision: int) -> float:

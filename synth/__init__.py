@@ -137,7 +137,7 @@ def simulate(seed: int, G: int, coverage: float, L: int, err: float, n_rate: flo
 # --------------------------------------------------------------------------------------
 
 SEEDS = {"plain_1m": 0x5EED0001, "bacterial_5m": 0x5EED0002, "large_200m": 0x5EED0003,
-         "batched_64": 0x5EED0004, "served_500": 0x5EED0005}
+         "batched_64": 0x5EED0004, "served_500": 0x5EED0005, "satellite_50m": 0x5EED0006}
 
 WORKLOADS = {
     # 1 Mbp genome, 30x of 150 bp, 0.5 % errors, k=31, min depth 2, Q20
@@ -166,6 +166,38 @@ def workload(name: str, scale: float = 1.0, threads: int | None = None) -> ReadS
     rs.meta["workload"] = name
     rs.meta["scale"] = scale
     rs.meta["params"] = dict(params)
+    return rs
+
+
+def concat(parts: list[ReadSet]) -> ReadSet:
+    """Read sets one after the other (offsets rebased)."""
+    seq = np.concatenate([p.seq for p in parts])
+    qual = np.concatenate([p.qual for p in parts])
+    offs = [np.zeros(1, np.uint64)]
+    base = 0
+    for p in parts:
+        offs.append(p.offsets[1:] - p.offsets[0] + np.uint64(base))
+        base += p.n_bases
+    return ReadSet(seq, qual, np.concatenate(offs))
+
+
+def satellite_workload(scale: float = 1.0, threads: int | None = None) -> ReadSet:
+    """A genome with a tandem satellite (heavy hitters, Section 5.1: highly repetitive genomes
+    have k-mers seen millions of times): a 50 Mbp random genome (x scale) read at 30x of 150 bp
+    with 1 % errors, and as many reads again x 3/7 from a 100 kbp array of one 171-bp unit
+    (an alpha-satellite-like period), so that 30 % of the reads are satellite; k = 31, min depth 2.
+    Each of the unit's 171 k-mers then occurs in about 0.2 % of the windows."""
+    seed = SEEDS["satellite_50m"]
+    G = max(int(50_000_000 * scale), 4000)
+    g, _ = genome(seed, G)
+    n_main = int(round(30 * G / 150))
+    main = reads_from_genome(seed ^ 0xA5A5, g, n_main, 150, 0.01, threads=threads)
+    unit = genome(seed ^ 0x5A7, 171)[0]
+    arr = np.ascontiguousarray(np.tile(unit, 100_000 // 171 + 1)[:100_000])
+    sat = reads_from_genome(seed ^ 0x5A75, arr, int(round(n_main * 3 / 7)), 150, 0.01, threads=threads)
+    rs = concat([main, sat])
+    rs.meta.update(dict(seed=seed, G=G, coverage=30 / 0.7, L=150, err=0.01, workload="satellite_50m",
+                        scale=scale, params=dict(k=31, min_depth=2, qual_threshold=20, bloom_fpr=0.01)))
     return rs
 
 

@@ -147,7 +147,7 @@ def test_partition_sizing(lib):
     big = _plan(k=51, max_bases=6_000_000_000, expected_distinct=2_100_000_000,
                 expected_keys=300_000_000)
     per_part = (big.bloom_words * 8 + big.table_slots * 64) / big.partitions
-    assert big.partitions > 1 and per_part <= 48 * 2**20 * 1.01
+    assert big.partitions > 1 and per_part <= 64 * 2**20 * 1.01
     assert big.bloom_words % big.partitions == 0 and big.table_slots % big.partitions == 0
     forced = _plan(k=31, max_bases=1_000_000, partitions=7)
     assert forced.partitions == 7 and forced.table_slots % 7 == 0
@@ -200,3 +200,31 @@ def test_host_result_buffers_layout():
     assert ext.shape == (5, 8) and ext.dtype == np.uint32
     assert codes.shape == (5, 2) and codes.dtype == np.uint8
     assert all(a.flags.c_contiguous for a in (keys, counts, ext, codes))
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets of the C header's
+    (checked by compiling a small C program against include/kmer_analysis.h)."""
+    import shutil
+    import subprocess
+    from paper_1705_11147_gb300 import capi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [capi.kma_params, capi.kma_plan, capi.kma_result, capi.kma_timings, capi.kma_contigs,
+               capi.kma_estimate, capi.kma_reads]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kmer_analysis.h"', "int main(void) {"]
+    for st in structs:
+        lines.append(f'  printf("{st.__name__} size %zu\\n", sizeof({st.__name__}));')
+        for name, *_ in st._fields_:
+            lines.append(f'  printf("{st.__name__} {name} %zu\\n", offsetof({st.__name__}, {name}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o", str(exe)])
+    out = dict(line.rsplit(" ", 1) for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for st in structs:
+        assert int(out[f"{st.__name__} size"]) == ctypes.sizeof(st), st.__name__
+        for name, *_ in st._fields_:
+            assert int(out[f"{st.__name__} {name}"]) == getattr(st, name).offset, (st.__name__, name)

@@ -436,6 +436,79 @@ def test_hll_registers_match_oracle(gpu, k, canonical, p):
     assert abs(est.distinct - n) <= 4 * est.rel_std_error * n + 2, (est.distinct, n)
 
 
+def _check_heavy_summary(est, rs, k, canonical=True):
+    """The merged Misra-Gries summaries of the cardinality pass against the exact sampled
+    stream (oracle): the same sub-stream sizes, every key in its own sub-stream, and per
+    sub-stream of n items the Misra-Gries bound: f - n/(m+1) <= c <= f for every key (c = 0
+    if absent), every key with f > n/(m+1) present."""
+    from paper_1705_11147_gb300 import capi
+    stream = oracle.sampled_stream(rs.seq, rs.qual, rs.offsets, k=k, canonical=canonical)
+    bucket = oracle.stream_bucket(stream, 5)
+    assert est.sampled_windows == len(stream)
+    np.testing.assert_array_equal(est.bucket_windows, np.bincount(bucket, minlength=capi.MG_BUCKETS))
+    if len(est.summary_keys):
+        np.testing.assert_array_equal(est.summary_bucket, oracle.stream_bucket(est.summary_keys, 5))
+    got = {(int(a), int(b)): int(c) for (a, b), c in zip(est.summary_keys, est.summary_counts)}
+    assert len(got) == len(est.summary_keys)
+    keys, inv, freq = np.unique(stream.view([("lo", np.uint64), ("hi", np.uint64)]).ravel(), return_inverse=True,
+                                return_counts=True)
+    kb = np.zeros(len(keys), np.int64)
+    kb[inv] = bucket
+    for (lo_hi, f, b) in zip(keys, freq, kb):
+        key = (int(lo_hi["lo"]), int(lo_hi["hi"]))
+        eps = int(est.bucket_windows[b]) / (capi.MG_COUNTERS + 1)
+        c = got.get(key, 0)
+        assert f - eps <= c <= f, (key, f, c, eps)
+        if f > eps:
+            assert key in got
+    assert set(got) <= {(int(x["lo"]), int(x["hi"])) for x in keys}
+    return got, freq
+
+
+def test_heavy_hitter_summaries(gpu):
+    """Cardinality pass with the heavy-hitter summaries (Section 5.1): few distinct keys ->
+    the summaries are the exact sampled frequencies; a satellite in a third of the reads ->
+    its k-mers are found and heavy_hitters is recommended; uniform reads -> no heavy hitters.
+    The read sets whose count runs with the recommended setting give the oracle's records."""
+    from paper_1705_11147_gb300 import estimate_distinct
+    rng = np.random.default_rng(31)
+    # three reads repeated: at most a few dozen distinct sampled keys per sub-stream
+    base = ["".join("ACGT"[i] for i in rng.integers(0, 4, 100)) for _ in range(3)]
+    rs = readset([base[i % 3] for i in range(1500)], k=31, min_depth=2)
+    est = estimate_distinct(rs.seq, rs.qual, rs.offsets, k=31)
+    got, freq = _check_heavy_summary(est, rs, 31)
+    stream = oracle.sampled_stream(rs.seq, rs.qual, rs.offsets, k=31)
+    want = {(int(a), int(b)): 0 for a, b in stream}
+    for a, b in stream:
+        want[(int(a), int(b))] += 1
+    assert got == want  # exact: no sub-stream ever exceeded its counters
+    # satellite of period 171 in a third of the reads (as in the heavy-hitter grouping test)
+    unit = "".join("ACGT"[i] for i in rng.integers(0, 4, 171))
+    g = "".join("ACGT"[i] for i in rng.integers(0, 4, 200_000))
+    sat, reads = unit * 60, []
+    for i in range(6000):
+        src = sat if i % 3 == 0 else g
+        a = int(rng.integers(0, len(src) - 150))
+        r = src[a:a + 150]
+        reads.append(r if i % 2 else r.translate(str.maketrans("ACGT", "TGCA"))[::-1])
+    rs = readset(reads, k=31, min_depth=2, min_ext_count=2, qual_threshold=20)
+    for dev in (False, True):
+        args = to_dev(gpu, rs) if dev else (rs.seq, rs.qual, rs.offsets)
+        est = estimate_distinct(*args, k=31)
+        _check_heavy_summary(est, rs, 31)
+        assert est.heavy_hitters
+    unit_keys = {min(w, w.translate(str.maketrans("ACGT", "TGCA"))[::-1])
+                 for w in ((unit * 2)[i:i + 31] for i in range(171))}
+    top = set(oracle.unpack(est.summary_keys[est.summary_counts >= est.heavy_threshold], 31))
+    assert top and top <= unit_keys
+    assert_same(run_gpu(gpu, rs, heavy_hitters=est.heavy_hitters, partitions=4), oracle_for(rs), "satellite")
+    # uniform random genome: nothing frequent
+    rp = synth.workload("plain_1m", scale=0.1)
+    est = estimate_distinct(rp.seq, rp.qual, rp.offsets, k=31)
+    _check_heavy_summary(est, rp, 31)
+    assert not est.heavy_hitters
+
+
 def test_hll_plain_1m_device_host_and_merge(gpu, plain):
     """Same sketch from host and device inputs; sketches of two halves merge (elementwise
     maximum) into the sketch of the whole; owner partitions of three 'GPUs' merge likewise."""

@@ -457,3 +457,83 @@ def test_contig_vertices_used_once():
             w = c[i:i + 31]
             seen.append(min(w, _revcomp(w)))
     assert len(seen) == len(set(seen)) == len(vertices) and set(seen) == vertices
+
+
+# ------------------------------------------------------------------ heavy hitters (Misra-Gries)
+
+def _exact_counts(stream):
+    keys, counts = np.unique(np.ascontiguousarray(stream).view([("lo", np.uint64), ("hi", np.uint64)]).ravel(),
+                             return_counts=True)
+    return {(int(k["lo"]), int(k["hi"])): int(c) for k, c in zip(keys, counts)}
+
+
+def test_misra_gries_worked_example():
+    """By hand, m = 2: AAA CCC AAA GGG AAA -> {AAA:1, CCC:1} after three items' updates, GGG
+    finds no free counter (both decrement: AAA 1, CCC 0), the last AAA raises AAA to 2."""
+    keys, counts = oracle.misra_gries(oracle.pack(["AAA", "CCC", "AAA", "GGG", "AAA"]), 2)
+    assert oracle.unpack(keys, 3) == ["AAA"] and list(counts) == [2]
+
+
+def test_misra_gries_exact_with_few_keys_and_bound_otherwise():
+    """With at most m distinct keys no decrement ever happens: the summary is the exact
+    frequency table. With more, every key of frequency f > n/(m+1) is kept with a count c,
+    f - n/(m+1) <= c <= f, and a key left out has f <= n/(m+1) (Misra and Gries 1982)."""
+    rng = np.random.default_rng(7)
+    for trial in range(30):
+        m = int(rng.integers(2, 12))
+        n_keys = int(rng.integers(1, m + 1))
+        pool = rng.integers(0, 2**40, (n_keys, 2), dtype=np.uint64)
+        stream = pool[rng.integers(0, n_keys, int(rng.integers(1, 400)))]
+        keys, counts = oracle.misra_gries(stream, m)
+        got = {(int(a), int(b)): int(c) for (a, b), c in zip(keys, counts)}
+        assert got == _exact_counts(stream)
+    for trial in range(40):
+        m = int(rng.integers(2, 16))
+        n = int(rng.integers(50, 3000))
+        heavy = rng.integers(0, 2**40, (3, 2), dtype=np.uint64)
+        noise = rng.integers(0, 2**40, (n, 2), dtype=np.uint64)
+        pick = rng.random(n)
+        stream = np.where((pick < 0.5)[:, None], heavy[rng.integers(0, 3, n)], noise)
+        keys, counts = oracle.misra_gries(stream, m)
+        got = {(int(a), int(b)): int(c) for (a, b), c in zip(keys, counts)}
+        exact = _exact_counts(stream)
+        eps = n / (m + 1)
+        assert len(got) <= m
+        for key, f in exact.items():
+            c = got.get(key, 0)
+            assert f - eps <= c <= f
+            if f > eps:
+                assert key in got
+
+
+def test_sampled_stream_by_brute_force():
+    """The sampled stream: windows starting at every 16th position of the reads laid out with
+    one separator per read, canonical keys, invalid windows skipped; brute force on strings."""
+    rng = np.random.default_rng(11)
+    reads = ["".join(rng.choice(list("ACGTACGTNacgt"), int(rng.integers(0, 70)))) for _ in range(300)]
+    seq, qual, offs = oracle.reads_from_strings(reads)
+    tr = str.maketrans("ACGT", "TGCA")
+    for k, canonical in ((5, True), (21, True), (6, False)):
+        want, pos = [], 0
+        for r in reads:
+            up = r.upper()
+            for i in range(len(r) - k + 1):
+                w = up[i:i + k]
+                if (pos + i) % 16 == 0 and set(w) <= set("ACGT"):
+                    rc = w.translate(tr)[::-1]
+                    want.append(min(w, rc) if canonical else w)
+            pos += len(r) + 1
+        got = oracle.unpack(oracle.sampled_stream(seq, qual, offs, k=k, canonical=canonical), k)
+        assert got == want
+
+
+def test_stream_bucket_is_the_sketch_register_prefix():
+    """The sub-stream of a key is the top 5 bits of the sketch hash: the register index a
+    one-key HyperLogLog sketch of precision 14 sets, shifted right by 9."""
+    rng = np.random.default_rng(5)
+    keys = rng.integers(0, 2**62, (200, 2), dtype=np.uint64)
+    b = oracle.stream_bucket(keys, 5)
+    for i in range(keys.shape[0]):
+        regs = oracle.hll_registers(keys[i:i + 1], 14)
+        assert int(np.nonzero(regs)[0][0]) >> 9 == int(b[i])
+    assert len(np.unique(oracle.stream_bucket(rng.integers(0, 2**62, (20000, 2), dtype=np.uint64), 5))) == 32
