@@ -573,13 +573,15 @@ def run_batched(args, ws, rank, local):
         h.destroy()
     del g
 
-    # plain: one job per launch sequence, sample after sample
+    # plain: one job per launch sequence, sample after sample (parameters worked out before
+    # the timed loop, as for the batched path: only library work is timed)
     stream = torch.cuda.current_stream(dev)
+    plain_params = [params(rs) for rs in sets]
 
     def plain_once():
         n = 0
-        for rs, (sq, ql, of) in zip(sets, reads):
-            with KmerAnalysis(params(rs), stream=stream) as ka:
+        for prm, (sq, ql, of) in zip(plain_params, reads):
+            with KmerAnalysis(prm, stream=stream) as ka:
                 ka.count(sq, ql, of)
                 n += int(ka.finalize().valid_windows)
         return n
@@ -610,13 +612,16 @@ def run_batched(args, ws, rank, local):
 
 # ------------------------------------------------------------------ served (job stream)
 
-def records_equal(a, b) -> bool:
-    """Two results hold the same records (keys, counts, extension counters, side codes),
-    compared after sorting by key."""
-    if len(a) != len(b):
-        return False
-    a, b = a.sorted(), b.sorted()
-    return all(np.array_equal(getattr(a, f), getattr(b, f)) for f in ("keys", "counts", "ext", "codes"))
+def records_digest(r) -> str:
+    """Digest of a result's records (keys, counts, extension counters, side codes) sorted by
+    key: two results hold the same records iff their digests are equal (up to SHA-256
+    collisions), without keeping the records."""
+    import hashlib
+    s = r.sorted()
+    h = hashlib.sha256()
+    for f in ("keys", "counts", "ext", "codes"):
+        h.update(np.ascontiguousarray(getattr(s, f)).tobytes())
+    return h.hexdigest()
 
 
 def run_served(args, ws, rank, local):
@@ -639,20 +644,36 @@ def run_served(args, ws, rank, local):
     t_gen = time.perf_counter() - t_gen
 
     def saturate():
+        # results are reduced to their window counts as they complete (the records of all
+        # jobs would not fit in host memory at the larger scales); digests are taken after
+        # the timed region
         with Server(max_batch=args.max_batch, workers=args.workers) as srv:
             t0 = time.perf_counter()
             futs = [srv.submit(j) for j in jobs]
-            res = [f.result() for f in futs]
+            windows = []
+            for i in range(len(futs)):
+                windows.append(int(futs[i].result().valid_windows))
+                futs[i] = None  # the records are not kept
             dt = time.perf_counter() - t0
-        return dt, res, srv.batches
+        return dt, windows, srv.batches
 
     saturate()  # warm-up (pools, module load)
-    t_srv, res_srv, batches = saturate()
+    t_srv, win_srv, batches = saturate()
     t0 = time.perf_counter()
-    res_plain = run_plain(jobs)
+    win_plain = [int(r.valid_windows) for r in run_plain(jobs, keep=False)]
     t_plain = time.perf_counter() - t0
-    windows = sum(int(r.valid_windows) for r in res_srv)
-    same = all(records_equal(a, b) for a, b in zip(res_srv, res_plain))
+    windows = sum(win_srv)
+    assert win_srv == win_plain
+    # every served job's records against its plain run, job by job (outside the timed region)
+    n_check = min(len(jobs), args.check_jobs)
+    with Server(max_batch=args.max_batch, workers=args.workers) as srv:
+        futs = [srv.submit(j) for j in jobs[:n_check]]
+        dig_srv = []
+        for i in range(len(futs)):
+            dig_srv.append(records_digest(futs[i].result()))
+            futs[i] = None
+    dig_plain = [records_digest(r) for r in run_plain(jobs[:n_check], keep=True, lazy=True)]
+    same = dig_srv == dig_plain
     # latency under Poisson arrivals (arrival times of the first jobs, in real time)
     n_lat = min(len(jobs), args.latency_jobs)
     with Server(max_batch=args.max_batch, workers=args.workers) as srv:
@@ -678,7 +699,7 @@ def run_served(args, ws, rank, local):
             "plain": {"value": round(plain_value, 3), "unit": UNIT, "seconds": round(t_plain, 3),
                       "path": "create -> count (host reads) -> finalize -> copy -> destroy, one job at a time"},
             "served_vs_plain": round(value / plain_value, 3), "batches": batches,
-            "records_match_plain": bool(same),
+            "records_match_plain": bool(same), "records_checked_jobs": n_check,
             "latency": {"jobs": n_lat, "rate_per_s": 4.0, **lat}, "generation_s": round(t_gen, 1)}
 
 
@@ -803,6 +824,7 @@ def main():
     ap.add_argument("--samples", type=int, default=64)
     ap.add_argument("--jobs", type=int, default=500)
     ap.add_argument("--latency-jobs", type=int, default=60)
+    ap.add_argument("--check-jobs", type=int, default=500)
     ap.add_argument("--max-batch", type=int, default=16)
     ap.add_argument("--workers", type=int, default=3)
     ap.add_argument("--scale", type=float, default=1.0)

@@ -303,6 +303,18 @@ __device__ __forceinline__ void rec_issue(WarpStage<KW, RPT>& S, const PartRecor
   tma_load_1d_hint(smem_u32(S.info[buf]), R.info + base, n16, bar, pol);
 }
 
+// Lane 0: the same staging copy into explicit buffers (keys, info) completing on `bar`.
+template <int KW>
+__device__ __forceinline__ void rec_issue_raw(u64* keys, unsigned char* info, unsigned bar, const PartRecords& R,
+                                              u64 base, unsigned n, u64 pol) {
+  const unsigned n16 = (n + 15u) & ~15u;
+  const unsigned kb = n16 * 8u * KW;
+  fence_proxy_async_smem();
+  mbar_expect_tx(bar, kb + n16);
+  tma_load_1d_hint(smem_u32(keys), reinterpret_cast<const u64*>(R.keys) + base * KW, kb, bar, pol);
+  tma_load_1d_hint(smem_u32(info), R.info + base, n16, bar, pol);
+}
+
 __device__ __forceinline__ u64 shfl0(u64 v) { return __shfl_sync(0xffffffffu, v, 0); }
 
 template <int KW, int RPT, unsigned MODE, bool GROUP>
@@ -535,6 +547,140 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
   }
 }
 
+// ------------------------------------------------------------------ recount
+//
+// The first sightings marked by the Bloom pass (about two in five records, most of them k-mers
+// seen once) are added to the k-mers that reached the table. Every warp stages its tiles like
+// the other record passes, copies each tile's marked records into a ring in shared memory
+// (the staging buffer is then free for the next copy), and resolves the ring in full rounds of
+// 32 records, one per lane: key filter, then (for the few that pass it) the table probe and the
+// count. Resolving tile by tile instead would leave most lanes idle in every round.
+
+constexpr int kRing = 128;  // entries; a tile adds at most 64 to fewer than 32 left over
+
+template <int KW>
+struct RecountStage {
+  static constexpr int kTile = 64;
+  u64 keys[2][kTile * KW];
+  u64 rkeys[kRing * KW];
+  unsigned char info[2][kTile];
+  unsigned char rinfo[kRing];
+  unsigned long long bar[2];
+};
+static_assert(sizeof(RecountStage<1>) % 16 == 0 && sizeof(RecountStage<2>) % 16 == 0,
+              "every warp's staging buffers must start on a 16-byte boundary");
+
+// One round: lane l resolves ring entry (head + l), if act.
+template <int KW>
+__device__ __forceinline__ void recount_round(const PartGeom& G, const RecountStage<KW>& S, unsigned e, bool act) {
+  if (!act) return;
+  Window w;
+  if (KW == 1) {
+    w.lo = S.rkeys[e];
+    w.hi = 0;
+  } else {
+    const ulonglong2 kk = reinterpret_cast<const ulonglong2*>(S.rkeys)[e];
+    w.lo = kk.x;
+    w.hi = kk.y;
+  }
+  window_of(S.rinfo[e], w);
+  const u64 h = key_hash(w.lo, w.hi);
+  const unsigned p = part_of(h, G.P);
+  // most first sightings are of k-mers seen once, which never reached the table: the key
+  // filter (every inserted key set its bits) rules them out without a probe
+  if (G.Wk) {
+    const u64 m = keyfilter_mask(h, G.bloom_h);
+    if ((__ldcg(G.keyfilter + (u64)p * G.Wk + keyfilter_index(h, G.Wk)) & m) != m) return;
+  }
+  Slot* sub = G.table + (u64)p * G.Sp;
+  const u64 idx = table_index(h, G.Sp);
+  const ulonglong2 kv = __ldcg(reinterpret_cast<const ulonglong2*>(sub + idx));
+  bool full;
+  Slot* s = resolve_find(sub, G.Sp, idx, kv, w.lo, w.hi, full);
+  if (full) atomicOr(&G.status->flags, kFlagFull);
+  if (s) {
+    if (G.no_overflow) add_occurrence_red(s, w);
+    else add_occurrence(s, w, 1u, G.status);
+  }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(kPartThreads, 5) part_recount_kernel(const __grid_constant__ PartGeom G,
+                                                                    const __grid_constant__ PartRecords R) {
+  constexpr int kTile = RecountStage<KW>::kTile;
+  constexpr int kWarps = kPartThreads / 32;
+  __shared__ __align__(128) RecountStage<KW> stage[kWarps];
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  RecountStage<KW>& S = stage[warp];
+  const unsigned tpb = (unsigned)((R.cap + kTile - 1) / kTile);
+  const unsigned ofill = (unsigned)(R.fill[G.P] < R.ocap ? R.fill[G.P] : R.ocap);
+  const unsigned nb = (R.p_end - R.p_begin) * tpb;
+  const unsigned n_tiles = nb + (R.overflow ? (ofill + kTile - 1) / kTile : 0u);
+  const u64 pol = policy_evict_first();
+  unsigned phases = 0;
+  unsigned head = 0, tail = 0;  // ring: entries [head, tail) are waiting (same in every lane)
+
+  unsigned t = 0, cb = ~0u, cf = 0, c_end = 0, c_next = 0;
+  u64 base = 0;
+  unsigned n = 0;
+  if (lane == 0) {
+    mbar_init(smem_u32(&S.bar[0]), 1);
+    mbar_init(smem_u32(&S.bar[1]), 1);
+    c_next = atomicAdd(R.queue, 1u);
+    n = rec_next<kTile>(G, R, tpb, nb, n_tiles, t, c_end, c_next, base, cb, cf);
+    if (n) rec_issue_raw<KW>(S.keys[0], S.info[0], smem_u32(&S.bar[0]), R, base, n, pol);
+  }
+  __syncwarp();
+  n = __shfl_sync(0xffffffffu, n, 0);
+  base = shfl0(base);
+  int buf = 0;
+  while (n) {
+    u64 nbase = 0;
+    unsigned nn = 0;
+    if (lane == 0) {
+      nn = rec_next<kTile>(G, R, tpb, nb, n_tiles, t, c_end, c_next, nbase, cb, cf);
+      if (nn) rec_issue_raw<KW>(S.keys[buf ^ 1], S.info[buf ^ 1], smem_u32(&S.bar[buf ^ 1]), R, nbase, nn, pol);
+    }
+    nn = __shfl_sync(0xffffffffu, nn, 0);
+    nbase = shfl0(nbase);
+    const unsigned bar = smem_u32(&S.bar[buf]);
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, (phases >> buf) & 1u, G.wait_limit));
+    if (!ok) {  // give up: report, let the copies in flight land (bounded), stop the warp
+      if (lane == 0) {
+        atomicOr(&G.status->flags, kFlagTimeout);
+        mbar_drain(bar, (phases >> buf) & 1u, G.wait_limit);
+        if (nn) mbar_drain(smem_u32(&S.bar[buf ^ 1]), (phases >> (buf ^ 1)) & 1u, G.wait_limit);
+      }
+      return;
+    }
+    phases ^= 1u << buf;
+    // the tile's marked records into the ring
+#pragma unroll
+    for (int j = 0; j < kTile / 32; ++j) {
+      const unsigned i = j * 32 + lane;
+      const bool f = i < n && (S.info[buf][i] & kInfoFirst);
+      const unsigned m = __ballot_sync(0xffffffffu, f);
+      if (f) {
+        const unsigned e = (tail + __popc(m & ((1u << lane) - 1u))) & (kRing - 1);
+        if (KW == 1) S.rkeys[e] = S.keys[buf][i];
+        else reinterpret_cast<ulonglong2*>(S.rkeys)[e] = reinterpret_cast<const ulonglong2*>(S.keys[buf])[i];
+        S.rinfo[e] = S.info[buf][i];
+      }
+      tail += __popc(m);
+    }
+    __syncwarp();  // ring entries visible to every lane; buffer `buf` free for the next copy
+    while (tail - head >= 32) {
+      recount_round<KW>(G, S, (head + lane) & (kRing - 1), true);
+      head += 32;
+    }
+    __syncwarp();  // ring slots are rewritten by the next tile
+    n = nn;
+    base = nbase;
+    buf ^= 1;
+  }
+  recount_round<KW>(G, S, (head + lane) & (kRing - 1), lane < tail - head);
+}
+
 // ------------------------------------------------------------------ key filter
 //
 // After the Bloom pass: every key in the table sets its bits in its partition's key filter.
@@ -608,6 +754,24 @@ static cudaError_t launch_pass_rt(const PartGeom& g, const PartRecords& r, cudaS
   return cudaGetLastError();
 }
 
+template <int KW>
+static cudaError_t launch_recount(const PartGeom& g, const PartRecords& r, cudaStream_t stream, int num_sms) {
+  constexpr int tile = RecountStage<KW>::kTile;
+  if (r.p_begin > r.p_end || r.p_end > g.P) return cudaErrorInvalidValue;
+  const u64 tiles = (u64)(r.p_end - r.p_begin) * ((r.cap + tile - 1) / tile) +
+                    (r.overflow ? (r.ocap + tile - 1) / tile : 0);
+  if (tiles == 0) return cudaSuccess;
+  if ((r.cap | r.ocap) & 15 || (reinterpret_cast<uintptr_t>(r.keys) | reinterpret_cast<uintptr_t>(r.info)) & 15)
+    return cudaErrorInvalidValue;  // staging needs 16-record buckets on 16-byte boundaries
+  const void* fn = (const void*)part_recount_kernel<KW>;
+  u64 grid = grid_for(fn, kPartThreads, 0, num_sms);
+  if (grid > tiles) grid = tiles;
+  cudaError_t e = cudaMemsetAsync(r.queue, 0, sizeof(unsigned), stream);  // the launch's tile queue
+  if (e != cudaSuccess) return e;
+  part_recount_kernel<KW><<<(unsigned)grid, kPartThreads, 0, stream>>>(g, r);
+  return cudaGetLastError();
+}
+
 template <int KW, int RPT>
 static cudaError_t launch_pass_mode(const PartGeom& g, const PartRecords& r, unsigned mode, cudaStream_t stream,
                                     int num_sms) {
@@ -619,7 +783,7 @@ static cudaError_t launch_pass_mode(const PartGeom& g, const PartRecords& r, uns
   if (mode == kModeCount)
     return group ? launch_pass_rt<KW, RPT, kModeCount, true>(g, r, stream, num_sms)
                  : launch_pass_rt<KW, RPT, kModeCount, false>(g, r, stream, num_sms);
-  return launch_pass_rt<KW, RPT, kModeRecount, false>(g, r, stream, num_sms);
+  return launch_recount<KW>(g, r, stream, num_sms);
 }
 
 cudaError_t launch_keyfilter_build(const PartGeom& g, cudaStream_t stream, int num_sms) {

@@ -49,10 +49,11 @@ class Job:
         return int(self.offsets.shape[0] - 1)
 
     def kma_params(self) -> capi.kma_params:
+        """Counting parameters of the job; the library chooses one table or on-chip partitions
+        from the job's size (kmer_analysis_plan), as for any handle."""
         p = dict(self.params)
         p.setdefault("max_bases", max(self.n_bases, 1))
         p.setdefault("max_reads", max(self.n_reads, 1))
-        p.setdefault("partitions", 1)
         return make_params(**p)
 
 
@@ -207,13 +208,20 @@ class Server:
                 "batches": self.batches}
 
 
-def run_plain(jobs: list[Job], device: int = 0) -> list[Result]:
+def run_plain(jobs: list[Job], device: int = 0, keep: bool = True, lazy: bool = False):
     """The plain path: one job at a time, create -> count (host reads) -> finalize -> copy
-    the records -> destroy."""
-    out = []
-    for j in jobs:
+    the records -> destroy. Returns the results (keep=False: the results without their
+    records, only the sizes; lazy=True: a generator, one job's records in memory at a time)."""
+    def one(j):
         with KmerAnalysis(j.kma_params()) as ka:
             ka.count(j.seq, j.qual, j.offsets)
-            ka.finalize()
-            out.append(ka.copy_result())
-    return out
+            info = ka.finalize()
+            r = ka.copy_result()
+            if not keep:
+                empty = np.zeros((0, 2), np.uint64)
+                r = Result(empty, np.zeros(0, np.uint32), np.zeros((0, 8), np.uint32),
+                           np.zeros((0, 2), np.uint8), int(info.n_uu), int(info.valid_windows),
+                           int(info.table_keys))
+            return r
+    gen = (one(j) for j in jobs)
+    return gen if lazy else list(gen)
