@@ -655,10 +655,10 @@ def run_served(args, ws, rank, local):
                 windows.append(int(futs[i].result().valid_windows))
                 futs[i] = None  # the records are not kept
             dt = time.perf_counter() - t0
-        return dt, windows, srv.batches
+        return dt, windows, srv.batches, {k2: round(v, 1) for k2, v in srv.phase_ms.items()}
 
     saturate()  # warm-up (pools, module load)
-    t_srv, win_srv, batches = saturate()
+    t_srv, win_srv, batches, phases = saturate()
     t0 = time.perf_counter()
     win_plain = [int(r.valid_windows) for r in run_plain(jobs, keep=False)]
     t_plain = time.perf_counter() - t0
@@ -700,6 +700,7 @@ def run_served(args, ws, rank, local):
                       "path": "create -> count (host reads) -> finalize -> copy -> destroy, one job at a time"},
             "served_vs_plain": round(value / plain_value, 3), "batches": batches,
             "records_match_plain": bool(same), "records_checked_jobs": n_check,
+            "server_phase_ms": phases,
             "latency": {"jobs": n_lat, "rate_per_s": 4.0, **lat}, "generation_s": round(t_gen, 1)}
 
 

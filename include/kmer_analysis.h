@@ -356,7 +356,7 @@ int kmer_analysis_copy_contigs(kma_handle* h, char* seq, uint64_t* offsets, int 
  * merged: counts of a key summed, the (m+1)-th largest subtracted): for a sub-stream of n
  * sampled windows, every key with sampled frequency f > n / (m + 1) is in the summary, with a
  * count c, f - n / (m + 1) <= c <= f; keys not in it have f <= n / (m + 1). */
-#define KMA_MG_SAMPLE 16
+#define KMA_MG_SAMPLE 64
 #define KMA_MG_BUCKETS 32
 #define KMA_MG_COUNTERS 32
 

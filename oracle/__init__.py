@@ -211,7 +211,7 @@ def hll_estimate(registers: np.ndarray, precision: int) -> float:
 
 
 def sampled_stream(seq: np.ndarray, qual: np.ndarray, offsets: np.ndarray, k: int, canonical: bool = True,
-                   sample: int = 16, **_) -> np.ndarray:
+                   sample: int = 64, **_) -> np.ndarray:
     """Keys (uint64[n, 2]) of the valid windows starting at every `sample`-th position of the
     reads laid out back to back with one separator after each read, in read order (the
     stream the heavy-hitter summaries of the cardinality pass are defined on)."""

@@ -73,7 +73,7 @@ class kma_estimate(ctypes.Structure):
 
 
 HLL_MIN_PRECISION, HLL_MAX_PRECISION = 4, 14
-MG_SAMPLE, MG_BUCKETS, MG_COUNTERS = 16, 32, 32
+MG_SAMPLE, MG_BUCKETS, MG_COUNTERS = 64, 32, 32
 
 
 class kma_reads(ctypes.Structure):

@@ -32,7 +32,7 @@ constexpr int kHllThreads = 512;
 constexpr int kHllWpt = 8;
 constexpr int kHllTile = kHllThreads * kHllWpt;
 constexpr int kHllWarps = kHllThreads / 32;
-constexpr int kMgItemsPerTile = kHllTile >> kMgSampleShift;  // at most one per 16 window starts
+constexpr int kMgItemsPerTile = kHllTile >> kMgSampleShift;  // at most one per 2^kMgSampleShift window starts
 static_assert(kMgCounters == 32 && kMgBuckets == 2 * kHllWarps, "one counter per lane, two buckets per warp");
 
 __host__ __device__ constexpr size_t hll_smem(unsigned p) {

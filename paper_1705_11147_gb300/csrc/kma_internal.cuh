@@ -246,7 +246,7 @@ int contig_pass(const unsigned long long* keys, const unsigned char* codes, unsi
 // Heavy-hitter summaries of the cardinality pass (kma_hll.cu): the windows at every
 // 2^kMgSampleShift-th arena position, split by the top kMgBucketBits bits of the key hash into
 // kMgBuckets sub-streams, one Misra-Gries summary of kMgCounters counters per sub-stream and CTA.
-constexpr unsigned kMgSampleShift = 4;
+constexpr unsigned kMgSampleShift = 6;
 constexpr unsigned kMgBucketBits = 5;
 constexpr unsigned kMgBuckets = 1u << kMgBucketBits;
 constexpr unsigned kMgCounters = 32;

@@ -80,6 +80,9 @@ class Server:
         self.done: list[Job] = []
         self.failures: list[tuple[Job, BaseException]] = []
         self.batches = 0
+        # host wall time of each phase of the batches, summed over the workers (ms)
+        self.phase_ms = {"copy_in": 0.0, "create": 0.0, "count": 0.0, "finalize": 0.0, "copy_out": 0.0,
+                         "release": 0.0}
         self.admit_hook = None  # testing: callable(job) that may raise to simulate failures
         self.threads = [threading.Thread(target=self._worker, daemon=True, name=f"kma-serve-{i}")
                         for i in range(workers)]
@@ -168,16 +171,24 @@ class Server:
                     if self.admit_hook is not None:
                         self.admit_hook(j)
                 dev = f"cuda:{self.device}"
+                tp = [time.perf_counter()]
                 with torch.cuda.stream(stream):
                     reads = [(torch.from_numpy(j.seq).to(dev), torch.from_numpy(j.qual).to(dev),
                               torch.from_numpy(j.offsets.view(np.int64)).to(dev)) for j in jobs]
+                    tp.append(time.perf_counter())
                     for j in jobs:
                         handles.append(KmerAnalysis(j.kma_params(), stream=stream))
+                    tp.append(time.perf_counter())
                     count_batch(handles, reads)
+                    tp.append(time.perf_counter())
                     finalize_batch(handles)
+                    tp.append(time.perf_counter())
                     results = [h.copy_result() for h in handles]
+                    tp.append(time.perf_counter())
                     del reads
                 t1 = time.perf_counter()
+                for name, a, b in zip(("copy_in", "create", "count", "finalize", "copy_out"), tp, tp[1:]):
+                    self.phase_ms[name] += (b - a) * 1e3
                 self.batches += 1
                 for j, fut, h, r in zip(jobs, [f for _, f in batch], handles, results):
                     j.t_done = t1
@@ -189,6 +200,7 @@ class Server:
                     self.done.append(j)
                 if not self.keep_resident:
                     self._release_budget(jobs)
+                self.phase_ms["release"] += (time.perf_counter() - t1) * 1e3
             except BaseException as e:  # a failed batch fails its jobs, the server goes on
                 for h in handles:
                     h.destroy()

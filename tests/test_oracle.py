@@ -506,9 +506,11 @@ def test_misra_gries_exact_with_few_keys_and_bound_otherwise():
                 assert key in got
 
 
-def test_sampled_stream_by_brute_force():
-    """The sampled stream: windows starting at every 16th position of the reads laid out with
-    one separator per read, canonical keys, invalid windows skipped; brute force on strings."""
+@pytest.mark.parametrize("sample", [16, 64])
+def test_sampled_stream_by_brute_force(sample):
+    """The sampled stream: windows starting at every `sample`-th position of the reads laid out
+    with one separator per read, canonical keys, invalid windows skipped; brute force on
+    strings."""
     rng = np.random.default_rng(11)
     reads = ["".join(rng.choice(list("ACGTACGTNacgt"), int(rng.integers(0, 70)))) for _ in range(300)]
     seq, qual, offs = oracle.reads_from_strings(reads)
@@ -519,11 +521,11 @@ def test_sampled_stream_by_brute_force():
             up = r.upper()
             for i in range(len(r) - k + 1):
                 w = up[i:i + k]
-                if (pos + i) % 16 == 0 and set(w) <= set("ACGT"):
+                if (pos + i) % sample == 0 and set(w) <= set("ACGT"):
                     rc = w.translate(tr)[::-1]
                     want.append(min(w, rc) if canonical else w)
             pos += len(r) + 1
-        got = oracle.unpack(oracle.sampled_stream(seq, qual, offs, k=k, canonical=canonical), k)
+        got = oracle.unpack(oracle.sampled_stream(seq, qual, offs, k=k, canonical=canonical, sample=sample), k)
         assert got == want
 
 
