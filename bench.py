@@ -486,6 +486,7 @@ def run_e2e(args, ka, rs, dev, qkeys_dev, ws):
     offs_np = offs_h.numpy().view(np.uint64)
 
     phases = {}
+    step_ms = []
 
     def step():
         # host wall time of each call (count returns once its input copies are done;
@@ -507,12 +508,14 @@ def run_e2e(args, ka, rs, dev, qkeys_dev, ws):
         t.append(time.perf_counter())
         for name, a, b in zip(("reset", "count", "finalize_to_host", "query"), t, t[1:]):
             phases[name] = round((b - a) * 1e3, 2)
+        step_ms.append(round((t[-1] - t[0]) * 1e3, 2))
         return r
 
     for _ in range(max(1, min(args.warmup, 2))):
         step()
     torch.cuda.synchronize(dev)
     barrier(ws)
+    step_ms.clear()
     t0 = time.perf_counter()
     steps = max(1, min(args.steps, 3))
     for _ in range(steps):
@@ -525,7 +528,7 @@ def run_e2e(args, ka, rs, dev, qkeys_dev, ws):
     d2h = n * (16 + 4 + 32 + 2) + qn * (4 + 32 + 2)
     return {"value": round(int(info.valid_windows) * (ws if ws > 1 else 1) / dt / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps,
-            "ms_per_step": round(dt * 1e3, 2), "last_step_phases_ms": phases}
+            "ms_per_step": round(dt * 1e3, 2), "last_step_phases_ms": phases, "step_host_ms": step_ms}
 
 
 # ------------------------------------------------------------------ batched (many samples)

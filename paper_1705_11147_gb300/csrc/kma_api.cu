@@ -253,6 +253,35 @@ void mg_merge(const std::vector<u64>& lo, const std::vector<u64>& hi, const std:
   std::stable_sort(out.begin(), out.end(), [](const MgEntry& x, const MgEntry& y) { return x.count > y.count; });
 }
 
+// Small pinned host blocks (a handle's status word and group counts), kept in a free list
+// for the life of the process: cudaFreeHost synchronises the whole device, so a handle
+// destroyed in one thread would otherwise stall the GPU work other threads have queued.
+constexpr size_t kPinnedBlock = 256;
+std::mutex g_pinned_mu;
+std::vector<void*> g_pinned_free;
+
+void* pinned_take() {
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  if (g_pinned_free.empty()) {
+    char* page = nullptr;
+    constexpr size_t kPerPage = 64;
+    if (cudaMallocHost((void**)&page, kPinnedBlock * kPerPage) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (size_t i = 0; i < kPerPage; ++i) g_pinned_free.push_back(page + i * kPinnedBlock);
+  }
+  void* b = g_pinned_free.back();
+  g_pinned_free.pop_back();
+  return b;
+}
+
+void pinned_give(void* b) {
+  if (!b) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free.push_back(b);
+}
+
 }  // namespace
 
 // finalize_to_host splits the recount and classification into this many groups of
@@ -405,9 +434,9 @@ void free_all(kma_handle* h) {
   dfree(h, h->out_keys); dfree(h, h->out_counts); dfree(h, h->out_ext); dfree(h, h->out_codes);
   free_contigs(h);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  if (h->host_status) cudaFreeHost(h->host_status);
+  pinned_give(h->host_status);
   h->host_status = nullptr;
-  if (h->host_groups) cudaFreeHost(h->host_groups);
+  pinned_give(h->host_groups);
   h->host_groups = nullptr;
   for (auto& e : h->group_ev) {
     if (e) cudaEventDestroy(e);
@@ -742,8 +771,10 @@ int kmer_analysis_create(const kma_params* params, void* cuda_stream, kma_handle
     delete h;
     return rc;
   }
-  e = cudaMallocHost((void**)&h->host_status, sizeof(DevStatus));
-  if (e != cudaSuccess) { free_all(h); delete h; return cuda_fail(e, "cudaMallocHost"); }
+  static_assert(sizeof(DevStatus) <= kPinnedBlock && kFinalizeGroups * sizeof(u64) <= kPinnedBlock,
+                "pinned blocks hold a status word and the group counts");
+  h->host_status = static_cast<DevStatus*>(pinned_take());
+  if (!h->host_status) { free_all(h); delete h; return KMA_ENOMEM; }
 
   std::memset(h->host_status, 0, sizeof(DevStatus));
   if ((rc = clear_state(h))) { free_all(h); delete h; return rc; }
@@ -1119,7 +1150,8 @@ int kmer_analysis_finalize_to_host(kma_handle* h, uint64_t* keys, uint32_t* coun
   if (!h) return KMA_EINVAL;
   if (h->finalized || h->failed) return KMA_ESTATE;
   if (!h->host_groups) {
-    KMA_CUDA(cudaMallocHost((void**)&h->host_groups, kFinalizeGroups * sizeof(u64)));
+    h->host_groups = static_cast<u64*>(pinned_take());
+    if (!h->host_groups) return KMA_ENOMEM;
     for (auto& e : h->group_ev) KMA_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   if (!h->copy_stream) KMA_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));

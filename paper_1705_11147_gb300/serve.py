@@ -158,6 +158,8 @@ class Server:
         torch = self.torch
         torch.cuda.set_device(self.device)
         stream = torch.cuda.Stream(self.device)
+        dev = f"cuda:{self.device}"
+
         while True:
             batch = self._admit()
             if not batch:
@@ -170,7 +172,6 @@ class Server:
                     j.t_start = t0
                     if self.admit_hook is not None:
                         self.admit_hook(j)
-                dev = f"cuda:{self.device}"
                 tp = [time.perf_counter()]
                 with torch.cuda.stream(stream):
                     reads = [(torch.from_numpy(j.seq).to(dev), torch.from_numpy(j.qual).to(dev),
