@@ -61,14 +61,22 @@ def workload_sizing(rs, n_parts: int = 1) -> dict:
                 expected_keys=int(keys * 1.25 / n_parts) + 1024)
 
 
-def make_handle_params(rs, n_parts=1, part=0, **tuning):
-    from paper_1705_11147_gb300 import make_params
+def handle_kwargs(rs, n_parts=1, part=0, tuned=True, **tuning):
+    """make_params keywords of the bench's handles, and where their launch tuning came from:
+    explicit keywords win, then the autotuner's choice for the job class (user cache, else the
+    table shipped with the package), else the library's automatic choices."""
+    from paper_1705_11147_gb300 import autotune
     p = rs.meta["params"]
-    size = workload_sizing(rs, n_parts)
-    return make_params(k=p["k"], min_depth=p["min_depth"], min_ext_count=2,
-                       qual_threshold=p["qual_threshold"], use_bloom=True,
-                       bloom_fpr=p.get("bloom_fpr", 0.01), max_bases=rs.n_bases,
-                       max_reads=rs.n_reads, n_parts=n_parts, part=part, **size, **tuning)
+    kw = dict(k=p["k"], min_depth=p["min_depth"], min_ext_count=2,
+              qual_threshold=p["qual_threshold"], use_bloom=True,
+              bloom_fpr=p.get("bloom_fpr", 0.01), max_bases=rs.n_bases,
+              max_reads=rs.n_reads, n_parts=n_parts, part=part, **workload_sizing(rs, n_parts), **tuning)
+    return autotune.apply(kw) if tuned else (kw, "none")
+
+
+def make_handle_params(rs, n_parts=1, part=0, tuned=True, **tuning):
+    from paper_1705_11147_gb300 import make_params
+    return make_params(**handle_kwargs(rs, n_parts, part, tuned, **tuning)[0])
 
 
 def run_large_once(rs, **tuning):
@@ -305,7 +313,11 @@ def run_ours(args, ws, rank, local):
     qual = torch.from_numpy(rs.qual).to(dev)
     offs = torch.from_numpy(rs.offsets.astype(np.int64)).to(dev)
     stream = torch.cuda.current_stream(dev)
-    prm = make_handle_params(rs, n_parts=ws, part=rank, **args.tuning)
+    if args.autotune:
+        autotune_workload(args, rs, seq, qual, offs, ws, rank)
+    hkw, tuning_source = handle_kwargs(rs, n_parts=ws, part=rank, **args.tuning)
+    from paper_1705_11147_gb300 import make_params
+    prm = make_params(**hkw)
     from paper_1705_11147_gb300 import plan as _plan
     plan_used = _plan(prm)
     ka = KmerAnalysis(prm, stream=stream)
@@ -449,7 +461,8 @@ def run_ours(args, ws, rank, local):
            "roofline": roof, "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
            "tuning": {k2: getattr(prm, k2) for k2 in ("block_threads", "windows_per_thread", "ctas_per_sm",
                                                       "warp_aggregate", "slot_prefetch", "partitions")}
-                     | {"partitions_used": int(plan_used.partitions)},
+                     | {"partitions_used": int(plan_used.partitions), "load_factor": round(prm.load_factor, 3),
+                        "source": tuning_source if not args.tuning else "command line"},
            "clocks": clk, "generation_s": round(t_gen, 1), "sizing_pass": sizing, "contigs": contigs}
     if e2e:
         out["e2e"] = e2e
@@ -532,6 +545,18 @@ def run_e2e(args, ka, rs, dev, qkeys_dev, ws):
 
 
 # ------------------------------------------------------------------ batched (many samples)
+
+def autotune_workload(args, rs, seq, qual, offs, ws, rank):
+    """Tune the handle's launch shape, load factor and partition count on this workload (device
+    tensors) and store the winner in `args.tune_out` (default: the user cache)."""
+    from paper_1705_11147_gb300 import autotune
+    base, _ = handle_kwargs(rs, n_parts=ws, part=rank, tuned=False)
+    t0 = time.perf_counter()
+    entry = autotune.tune(seq, qual, offs, base, reps=2, path=args.tune_out or None,
+                          log=lambda m: print(m, file=sys.stderr, flush=True), label=args.workload)
+    print(f"autotune: {entry['params']} {entry['ms']:.2f} ms ({time.perf_counter() - t0:.0f} s)",
+          file=sys.stderr, flush=True)
+
 
 def run_batched(args, ws, rank, local):
     """64 independent samples of uneven size: one captured CUDA graph per step (reset, one
@@ -839,6 +864,10 @@ def main():
     ap.add_argument("--tune", action="append", default=[],
                     help="launch-shape override key=value (block_threads, windows_per_thread, "
                          "ctas_per_sm, warp_aggregate, slot_prefetch, load_factor)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the autotuner's candidates on the workload first and store the winner")
+    ap.add_argument("--tune-out", default="",
+                    help="tuning table to write with --autotune (default: the user cache)")
     args = ap.parse_args()
     args.tuning = {}
     for kv in args.tune:

@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(kHllThreads) hll_kernel(const __grid_constant_
 
 unsigned hll_grid(unsigned p, int num_sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hll_kernel, kHllThreads, hll_smem(p)) != cudaSuccess) {
+  if (allow_dynamic_smem((const void*)hll_kernel, hll_smem(p)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hll_kernel, kHllThreads, hll_smem(p)) != cudaSuccess) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -160,7 +161,7 @@ cudaError_t launch_hll(const PartWindows& w, unsigned k, unsigned canonical, uns
                        unsigned p, unsigned* regs, DevStatus* st, const MgOut& mg, unsigned grid,
                        cudaStream_t stream) {
   const size_t smem = hll_smem(p);
-  cudaError_t e = cudaFuncSetAttribute(hll_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void*)hll_kernel, smem);
   if (e != cudaSuccess) return e;
   // every CTA runs (and writes its summaries) even when there are fewer tiles than CTAs
   hll_kernel<<<grid, kHllThreads, smem, stream>>>(w, k, canonical, n_parts, part, p, regs, st, mg);

@@ -261,6 +261,14 @@ struct MgOut {
   unsigned long long* items;
 };
 
+// Lets `fn` launch with up to the device's opt-in shared memory per block (less its static
+// shared memory) and checks that `need` dynamic bytes fit. The limit is a property of the
+// kernel, shared by every host thread: handles counting on several threads launch the same
+// kernel with different sizes, and a limit set to one launch's own size could be lowered by
+// another thread between that thread's set and its launch. So it is only ever set to the
+// maximum (once per kernel and device).
+cudaError_t allow_dynamic_smem(const void* fn, size_t need);
+
 // HyperLogLog registers (2^p, 32-bit each) of the windows [w.q0, w.q1), and the heavy-hitter
 // summaries of `grid` CTAs (kma_hll.cu); hll_grid gives the number of resident CTAs.
 unsigned hll_grid(unsigned p, int num_sms);

@@ -11,6 +11,10 @@
 //
 // The random atomics of one partition touch only its sub-filter and sub-table, sized to stay
 // resident in L2, instead of the whole multi-GB filter and table in HBM.
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "kma_device.cuh"
 
 namespace kma {
@@ -711,6 +715,29 @@ __global__ void __launch_bounds__(kKeyThreads) keyfilter_build_kernel(const __gr
 
 // ------------------------------------------------------------------ launchers
 
+cudaError_t allow_dynamic_smem(const void* fn, size_t need) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void*, int>, int>> done;  // (kernel, device) -> limit
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  int limit = -1;
+  for (const auto& d : done)
+    if (d.first.first == fn && d.first.second == dev) limit = d.second;
+  if (limit < 0) {
+    int optin = 0;
+    cudaFuncAttributes fa;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess)
+      return e;
+    limit = optin - (int)fa.sharedSizeBytes;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess) return e;
+    done.push_back({{fn, dev}, limit});
+  }
+  return need <= (size_t)limit ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 static int grid_for(const void* fn, int threads, size_t smem, int num_sms) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess) {
@@ -726,7 +753,7 @@ cudaError_t launch_part_scatter(const PartGeom& g, const PartWindows& w, const P
   const int kw = g.k > 32 ? 2 : 1;
   const size_t smem = scatter_smem(g.P, kw);
   const void* fn = kw == 2 ? (const void*)part_scatter_kernel<2> : (const void*)part_scatter_kernel<1>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem(fn, smem);
   if (e != cudaSuccess) return e;
   const u64 tiles = (w.q1 - w.q0 + kScatterTile - 1) / kScatterTile;
   u64 grid = grid_for(fn, kScatterThreads, smem, num_sms);

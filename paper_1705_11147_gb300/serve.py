@@ -3,9 +3,11 @@
 Jobs (host reads + counting parameters) are submitted at any time and return futures. They
 are admitted in arrival order while their device footprint (the handle's plan, the reads and
 the result records) fits the memory budget. Each worker thread owns a CUDA stream; when it is
-free it takes every admissible job that is waiting (up to `max_batch`) as one batch: the
-reads are copied in, all jobs of the batch are packed and counted by one launch each
-(kmer_analysis_count_batch) and finalized together (kmer_analysis_finalize_batch). While one
+free it takes every admissible job that is waiting (up to `max_batch`) as one batch: the small
+jobs' reads are copied in and packed and counted together (one launch each,
+kmer_analysis_count_batch), the large jobs are counted from host memory (kmer_analysis_count:
+staged copies overlapping the packing, in one call that releases the interpreter), and all are
+finalized together (kmer_analysis_finalize_batch). While one
 worker's batch is on the GPU the other workers copy in and launch the next jobs, so work of
 jobs that arrive while others run overlaps on the device. A finished job's table can stay
 resident for queries (`keep_resident`) until the caller releases it.
@@ -23,6 +25,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import capi
+from . import autotune
 from .kmer_analysis import KmerAnalysis, Result, count_batch, finalize_batch, make_params, plan
 
 
@@ -48,12 +51,15 @@ class Job:
     def n_reads(self) -> int:
         return int(self.offsets.shape[0] - 1)
 
-    def kma_params(self) -> capi.kma_params:
+    def kma_params(self, tuned: bool = True) -> capi.kma_params:
         """Counting parameters of the job; the library chooses one table or on-chip partitions
-        from the job's size (kmer_analysis_plan), as for any handle."""
+        from the job's size (kmer_analysis_plan), as for any handle. With `tuned`, the
+        autotuner's choice for the job's class fills in what the job's keywords leave open."""
         p = dict(self.params)
         p.setdefault("max_bases", max(self.n_bases, 1))
         p.setdefault("max_reads", max(self.n_reads, 1))
+        if tuned:
+            p, _ = autotune.apply(p)
         return make_params(**p)
 
 
@@ -62,7 +68,8 @@ class Server:
     jobs may hold (default: 80 % of the free memory at start)."""
 
     def __init__(self, device_budget: int | None = None, max_batch: int = 16, workers: int = 2,
-                 keep_resident: bool = False, device: int = 0):
+                 keep_resident: bool = False, device: int = 0, host_count_bases: int = 32 << 20,
+                 tuned: bool = True):
         import torch
         self.torch = torch
         self.device = device
@@ -73,6 +80,8 @@ class Server:
         self.budget = device_budget
         self.max_batch = min(max_batch, capi.KMA_MAX_BATCH)
         self.keep_resident = keep_resident
+        self.host_count_bases = host_count_bases  # jobs this large count from host memory
+        self.tuned = tuned                        # autotuner's choices per job class
         self.used = 0
         self.pending: deque[tuple[Job, Future]] = deque()
         self.cv = threading.Condition()
@@ -91,7 +100,7 @@ class Server:
 
     # ------------------------------------------------------------------ client side
     def footprint(self, job: Job) -> int:
-        pl = plan(job.kma_params())
+        pl = plan(job.kma_params(self.tuned))
         keys = int(job.params.get("expected_keys") or job.params.get("expected_distinct") or job.n_bases)
         return int(pl.device_bytes + 2 * job.n_bases + 8 * (job.n_reads + 1) + keys * 54)
 
@@ -174,13 +183,21 @@ class Server:
                         self.admit_hook(j)
                 tp = [time.perf_counter()]
                 with torch.cuda.stream(stream):
-                    reads = [(torch.from_numpy(j.seq).to(dev), torch.from_numpy(j.qual).to(dev),
-                              torch.from_numpy(j.offsets.view(np.int64)).to(dev)) for j in jobs]
+                    # small jobs: reads copied to the device and counted together (one packing
+                    # and one counting launch); large jobs: counted from host memory through the
+                    # library's staged copies (one call, so the copies of several workers overlap)
+                    small = [i for i, j in enumerate(jobs) if j.n_bases < self.host_count_bases]
+                    large = [i for i, j in enumerate(jobs) if j.n_bases >= self.host_count_bases]
+                    reads = [(torch.from_numpy(jobs[i].seq).to(dev), torch.from_numpy(jobs[i].qual).to(dev),
+                              torch.from_numpy(jobs[i].offsets.view(np.int64)).to(dev)) for i in small]
                     tp.append(time.perf_counter())
                     for j in jobs:
-                        handles.append(KmerAnalysis(j.kma_params(), stream=stream))
+                        handles.append(KmerAnalysis(j.kma_params(self.tuned), stream=stream))
                     tp.append(time.perf_counter())
-                    count_batch(handles, reads)
+                    if small:
+                        count_batch([handles[i] for i in small], reads)
+                    for i in large:
+                        handles[i].count(jobs[i].seq, jobs[i].qual, jobs[i].offsets)
                     tp.append(time.perf_counter())
                     finalize_batch(handles)
                     tp.append(time.perf_counter())
@@ -221,12 +238,12 @@ class Server:
                 "batches": self.batches}
 
 
-def run_plain(jobs: list[Job], device: int = 0, keep: bool = True, lazy: bool = False):
+def run_plain(jobs: list[Job], device: int = 0, keep: bool = True, lazy: bool = False, tuned: bool = True):
     """The plain path: one job at a time, create -> count (host reads) -> finalize -> copy
     the records -> destroy. Returns the results (keep=False: the results without their
     records, only the sizes; lazy=True: a generator, one job's records in memory at a time)."""
     def one(j):
-        with KmerAnalysis(j.kma_params()) as ka:
+        with KmerAnalysis(j.kma_params(tuned)) as ka:
             ka.count(j.seq, j.qual, j.offsets)
             info = ka.finalize()
             r = ka.copy_result()

@@ -29,6 +29,54 @@ def test_relative_partition_candidates():
     assert autotune.expand({"partitions": 5}, base)["partitions"] == 5
 
 
+def test_lookup_order_and_apply(tmp_path):
+    """User cache first, then the shipped table; tuned keywords fill only what the job leaves
+    open; relative partition counts resolve against the job's own automatic count, and a job
+    the library keeps in one table is not partitioned by a scale."""
+    from paper_1705_11147_gb300 import autotune, build, make_params, plan
+    build.build()
+    user = str(tmp_path / "user.json")
+    shipped = str(tmp_path / "shipped.json")
+    big = dict(k=51, max_bases=6_000_000_000, expected_distinct=2_100_000_000, expected_keys=300_000_000)
+    key = autotune.cache_key("GPU X", 51, big["max_bases"])
+    autotune.save_cache({key: {"params": {"partition_scale": 2.0, "load_factor": 0.6}}}, shipped)
+    got, src = autotune.lookup(51, big["max_bases"], gpu_name="GPU X", path=user, shipped=shipped)
+    assert src == "shipped" and got == {"partition_scale": 2.0, "load_factor": 0.6}
+    auto = plan(make_params(**{**big, "load_factor": 0.6})).partitions
+    kw, src = autotune.apply(dict(big), gpu_name="GPU X", path=user, shipped=shipped)
+    assert src == "shipped" and kw["load_factor"] == 0.6 and kw["partitions"] == min(2048, 2 * auto)
+    assert "partition_scale" not in kw
+    kw, _ = autotune.apply({**big, "partitions": 7, "load_factor": 0.5}, gpu_name="GPU X", path=user,
+                           shipped=shipped)
+    assert kw["partitions"] == 7 and kw["load_factor"] == 0.5
+    autotune.save_cache({key: {"params": {"windows_per_thread": 4}}}, user)
+    got, src = autotune.lookup(51, big["max_bases"], gpu_name="GPU X", path=user, shipped=shipped)
+    assert src == "cache" and got == {"windows_per_thread": 4}
+    assert autotune.lookup(31, big["max_bases"], gpu_name="GPU X", path=user, shipped=shipped) == ({}, "none")
+    # a one-table job stays one table under a partition scale
+    small = dict(k=31, max_bases=1 << 20, expected_distinct=1 << 16)
+    assert plan(make_params(**small)).partitions == 1
+    assert autotune.expand({"partition_scale": 0.5}, small)["partitions"] == 1
+    assert autotune.candidates_for(small) is autotune.DEFAULT_CANDIDATES
+    assert autotune.candidates_for(big) is autotune.PARTITIONED_CANDIDATES
+
+
+def test_shipped_table_is_valid():
+    """Every entry of the table shipped with the package names only tunable keywords with
+    values the library accepts."""
+    from paper_1705_11147_gb300 import autotune, build, make_params, plan
+    build.build()
+    table = autotune.load_cache(autotune.SHIPPED_TABLE)
+    for key, entry in table.items():
+        gpu, kw, cls = key.split("|")
+        assert kw in ("kw1", "kw2") and int(cls) >= 0 and gpu
+        assert set(entry["params"]) <= set(autotune.TUNABLE), entry
+        k = 51 if kw == "kw2" else 31
+        n = 1 << int(cls)
+        base = dict(k=k, max_bases=n, expected_distinct=n // 4)
+        plan(make_params(**autotune.expand({**entry["params"]}, base) | base))
+
+
 @pytest.mark.gpu
 def test_tune_on_gpu(tmp_path):
     torch = pytest.importorskip("torch")
@@ -45,5 +93,9 @@ def test_tune_on_gpu(tmp_path):
     cands = [dict(partitions=1, windows_per_thread=1), dict(partitions=1, windows_per_thread=2),
              dict(partitions=6), dict(partitions=-2, load_factor=0.7)]
     entry = autotune.tune(seq, qual, offs, base, candidates=cands, reps=1, path=path)
-    assert entry["params"] in [autotune.expand(c, base) for c in cands]
+    assert entry["params"] in cands
+    assert entry["resolved"] == autotune.expand(entry["params"], base)
     assert autotune.best(31, rs.n_bases, path=path) == entry["params"]
+    # the choice reaches a handle through apply(): explicit keywords win
+    kw, src = autotune.apply(dict(base), path=path, shipped=None)
+    assert src == "cache" and kw == {**base, **entry["resolved"]}
