@@ -386,69 +386,88 @@ __global__ void __launch_bounds__(kPackThreads, 4) pack_kernel(const __grid_cons
           const u64 mid = (lo + hi) >> 1;
           if (off[mid] - o0 + mid <= pos) lo = mid; else hi = mid;
         }
-        const unsigned rd0 = (unsigned)(lo - r0);  // read index relative to the chunk's first read
-        const unsigned snext0 = pack_next_start(off, o0, P0, nr, lo);
-        unsigned rd = rd0, snext = snext0;
+        unsigned rd = (unsigned)(lo - r0);  // read index relative to the chunk's first read
+        unsigned snext = pack_next_start(off, o0, P0, nr, lo);
         const unsigned nrd = (unsigned)(nr - r0);
         const unsigned* sw = reinterpret_cast<const unsigned*>(s_seq);
         const unsigned* qw = reinterpret_cast<const unsigned*>(s_qual);
         const unsigned qmin4 = (D.qual_min & 0xFFu) * 0x01010101u;
         const unsigned gmask = D.qual_min <= 0xFFu ? 0xFFFFFFFFu : 0u;
         const unsigned pw = (unsigned)(pos - P0);
-        // The 16 groups of four positions of the word, in a rotated order: lane l starts at
-        // group (l / 2) mod 16. Words of consecutive lanes are 64 staged bytes apart, so in the
-        // natural order every shared-memory load of a warp would fall into two of the 32 banks;
-        // rotated, the lanes' loads of one step fall into 32 different banks.
-        const unsigned g0 = (threadIdx.x >> 1) & 15u;
-        u64 c0 = 0, c1 = 0, rc0 = 0, rc1 = 0, inv = 0, hq = 0;
+        u64 c[2], rc[2], inv = 0, hq = 0;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          u64 cc = 0, qq = 0;
 #pragma unroll 2
-        for (unsigned k = 0; k < 16; ++k) {
-          const unsigned g = (g0 + k) & 15u;
-          if (g == 0 && k) {  // wrapped to the word's first group: back to its first read
-            rd = rd0;
-            snext = snext0;
-          }
-          const unsigned pg = pw + 4u * g;
-          while (rd < nrd && pg >= snext) snext = pack_next_start(off, o0, P0, nr, r0 + ++rd);
-          unsigned f8 = 0, r8 = 0, i4 = 0, h4 = 0;
-          const unsigned bi = pg - rd;  // staged byte of position pg, if it is a base
-          if (rd < nrd && pg + 4u < snext && bi + 4u <= nb) {
-            pack_group4(load4(sw, lead + bi), load4(qw, leadq + bi), qmin4, gmask, f8, r8, i4, h4);
-          } else {
-            unsigned rdi = rd, sni = snext;
-            for (unsigned i = 0; i < 4; ++i) {
-              const unsigned p = pg + i;
-              while (rdi < nrd && p >= sni) sni = pack_next_start(off, o0, P0, nr, r0 + ++rdi);
-              unsigned code = 0, valid = 0, good = 0;
-              const unsigned b = p - rdi;
-              if (rdi < nrd && p + 1u != sni && b < nb) {
-                const unsigned ch = s_seq[lead + b];
-                const unsigned u = (ch & 0xDFu) - 0x40u;  // A C G T (either case) -> bits 1 3 7 20
-                valid = u < 32u ? (0x10008Au >> u) & 1u : 0u;
-                code = valid ? ((ch >> 1) ^ (ch >> 2)) & 3u : 0u;  // A0 C1 G2 T3
-                good = valid && (unsigned)s_qual[leadq + b] >= D.qual_min;
+          for (int g = 0; g < 8; ++g) {
+            const unsigned pg = pw + 32u * half + 4u * g;
+            while (rd < nrd && pg >= snext) snext = pack_next_start(off, o0, P0, nr, r0 + ++rd);
+            // all four positions past the last read: invalid
+            unsigned f8 = 0, r8 = 0xFFu, i4 = 0xFu, h4 = 0;
+            if (rd < nrd) {
+              // A group holds at most one read separator (position snext - 1) unless a read is
+              // shorter than three bases. With the separator at s, the positions after it are
+              // the next read's bases, one byte earlier in the staged bytes: one byte permute
+              // of the group's four bytes, then position s (and, after the last read, the
+              // positions behind it) marked invalid. Every lane takes this path, so a warp
+              // does not diverge at read boundaries.
+              const unsigned bi = pg - rd;  // staged byte of position pg
+              const unsigned s = snext - 1u - pg;  // separator index in the group, >= 4: none
+              bool simple = bi + 4u <= nb;
+              unsigned rdn = rd, snn = snext;
+              if (s < 4u) {
+                rdn = rd + 1u;
+                snn = rdn < nrd ? pack_next_start(off, o0, P0, nr, r0 + rdn) : 0xFFFFFFFFu;
+                simple = bi + 3u <= nb && (rdn >= nrd || snn - 1u >= pg + 4u);
               }
-              f8 |= code << (6u - 2u * i);
-              r8 |= (~code & 3u) << (2u * i);
-              i4 |= (valid ^ 1u) << (3u - i);
-              h4 |= good << (3u - i);
+              if (simple) {
+                const unsigned ss = s < 4u ? s : 4u;
+                const unsigned sel = 0x3210u - (0x1110u & (0xFFF0u << (4u * ss)));
+                pack_group4(__byte_perm(load4(sw, lead + bi), 0u, sel), __byte_perm(load4(qw, leadq + bi), 0u, sel),
+                            qmin4, gmask, f8, r8, i4, h4);
+                if (s < 4u) {
+                  unsigned fm = 3u << (6u - 2u * s), rm = 3u << (2u * s), im = 1u << (3u - s);
+                  if (rdn >= nrd) {  // no read after the separator
+                    fm |= (1u << (6u - 2u * s)) - 1u;
+                    rm |= (0xFFu << (2u * s + 2u)) & 0xFFu;
+                    im |= (1u << (3u - s)) - 1u;
+                  }
+                  f8 &= ~fm;
+                  r8 |= rm;
+                  i4 |= im;
+                  h4 &= ~im;
+                  rd = rdn;
+                  snext = snn;
+                }
+              } else {  // reads shorter than three bases, or inconsistent offsets
+                f8 = 0, r8 = 0, i4 = 0, h4 = 0;
+                for (unsigned i = 0; i < 4; ++i) {
+                  const unsigned p = pg + i;
+                  while (rd < nrd && p >= snext) snext = pack_next_start(off, o0, P0, nr, r0 + ++rd);
+                  unsigned code = 0, valid = 0, good = 0;
+                  const unsigned b = p - rd;
+                  if (rd < nrd && p + 1u != snext && b < nb) {
+                    const unsigned ch = s_seq[lead + b];
+                    const unsigned u = (ch & 0xDFu) - 0x40u;  // A C G T (either case) -> bits 1 3 7 20
+                    valid = u < 32u ? (0x10008Au >> u) & 1u : 0u;
+                    code = valid ? ((ch >> 1) ^ (ch >> 2)) & 3u : 0u;  // A0 C1 G2 T3
+                    good = valid && (unsigned)s_qual[leadq + b] >= D.qual_min;
+                  }
+                  f8 |= code << (6u - 2u * i);
+                  r8 |= (~code & 3u) << (2u * i);
+                  i4 |= (valid ^ 1u) << (3u - i);
+                  h4 |= good << (3u - i);
+                }
+              }
             }
+            cc = (cc << 8) | f8;                // first position ends in the top bits
+            qq = (qq >> 8) | ((u64)r8 << 56);   // first position ends in the low bits
+            inv = (inv << 4) | i4;
+            hq = (hq << 4) | h4;
           }
-          // group g: forward codes first position in the top bits, complemented codes first
-          // position in the low bits, flags from bit 63 down
-          const unsigned gh = g & 7u;
-          const u64 fv = (u64)f8 << (56u - 8u * gh), rv = (u64)r8 << (8u * gh);
-          if (g < 8) {
-            c0 |= fv;
-            rc0 |= rv;
-          } else {
-            c1 |= fv;
-            rc1 |= rv;
-          }
-          inv |= (u64)i4 << (60u - 4u * g);
-          hq |= (u64)h4 << (60u - 4u * g);
+          c[half] = cc;
+          rc[half] = qq;
         }
-        const u64 c[2] = {c0, c1}, rc[2] = {rc0, rc1};
         reinterpret_cast<ulonglong2*>(D.codes)[gw] = make_ulonglong2(c[0], c[1]);
         reinterpret_cast<ulonglong2*>(D.rcodes)[gw] = make_ulonglong2(rc[0], rc[1]);
         D.inv[gw] = inv;
