@@ -34,6 +34,7 @@ int cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr u64 kArenaSlack = 64ull * 4096;  // padding positions for per-batch 64-alignment
+constexpr u64 kBatchSlack = 256;            // invalid positions kept behind the last batch
 constexpr u64 kDefaultStaging = 256ull << 20;
 
 // ------------------------------------------------------------------ Bloom sizing
@@ -455,6 +456,9 @@ void free_all(kma_handle* h) {
   h->event_pool.clear();
 }
 
+// Back to the empty state: status, Bloom filter, key filter and table cleared on the handle's
+// stream. The arena is not cleared: every count() rewrites the words of its batch and sets the
+// slack words behind it invalid (reserve_batch).
 int clear_state(kma_handle* h) {
   free_records(h);
   free_contigs(h);
@@ -464,12 +468,6 @@ int clear_state(kma_handle* h) {
   int rc = timed_launch(h, KMA_KERNEL_INIT, h->stream, h->d.plan.table_slots > 0,
                         [&] { return launch_table_init(h->table, h->d.plan.table_slots, h->stream); });
   if (rc) return rc;
-  // The arena is rewritten by each count(); only the slack words past the used range are
-  // read by windows near the end, and those must read as invalid.
-  KMA_CUDA(cudaMemsetAsync(h->inv, 0xFF, h->d.bit_words * 8, h->stream));
-  KMA_CUDA(cudaMemsetAsync(h->codes, 0, h->d.codes_words * 8, h->stream));
-  KMA_CUDA(cudaMemsetAsync(h->rcodes, 0xFF, h->d.codes_words * 8, h->stream));
-  KMA_CUDA(cudaMemsetAsync(h->hq, 0, h->d.bit_words * 8, h->stream));
   h->q_used = h->reads_used = h->bases_used = 0;
   h->count_bound = 0;
   h->finalized = false;
@@ -525,13 +523,23 @@ void set_pack_waits(kma_handle* h, PackBatch& pb) {
   pb.wait_limit = h->p.fault_inject == 1 ? kWaitPollsInjected : kWaitPolls;
 }
 
-// Reserve arena space for a batch and describe it for the pack kernel.
-int reserve_batch(kma_handle* h, u64 n_reads, u64 n_bases, PackDesc& pd, u64& q0, u64& n_pos) {
+// Reserve arena positions for a batch of n_reads reads (n_bases bases), packed on stream `st`,
+// and describe it for the pack kernel. The windows of the batch read up to 192 positions past
+// its end; the 256 positions behind it are set invalid here (ordered before the packing on
+// `st`), and the next batch's packing overwrites them.
+int reserve_batch(kma_handle* h, u64 n_reads, u64 n_bases, PackDesc& pd, u64& q0, u64& n_pos, cudaStream_t st) {
   n_pos = ((n_bases + n_reads + 63) / 64) * 64;
   if (n_pos == 0) n_pos = 64;
-  if (h->q_used + n_pos + 256 > h->d.plan.arena_positions) return KMA_EFULL;
+  if (h->q_used + n_pos + kBatchSlack > h->d.plan.arena_positions) return KMA_EFULL;
   if (h->bases_used + n_bases > h->p.max_bases) return KMA_EFULL;
   q0 = h->q_used;
+  {
+    const u64 e = q0 + n_pos;  // a multiple of 64
+    KMA_CUDA(cudaMemsetAsync(h->inv + e / 64, 0xFF, kBatchSlack / 64 * 8, st));
+    KMA_CUDA(cudaMemsetAsync(h->hq + e / 64, 0, kBatchSlack / 64 * 8, st));
+    KMA_CUDA(cudaMemsetAsync(h->codes + e / 32, 0, kBatchSlack / 32 * 8, st));
+    KMA_CUDA(cudaMemsetAsync(h->rcodes + e / 32, 0xFF, kBatchSlack / 32 * 8, st));
+  }
   std::memset(&pd, 0, sizeof(pd));
   pd.n_reads = n_reads; pd.n_bases = n_bases; pd.q0 = q0; pd.n_pos = n_pos;
   pd.codes = h->codes; pd.rcodes = h->rcodes; pd.inv = h->inv; pd.hq = h->hq; pd.status = h->status;
@@ -834,7 +842,7 @@ int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual, const 
     if (ends[1] < ends[0]) return KMA_EINVAL;
     PackDesc pd;
     u64 q0, n_pos;
-    if ((rc = reserve_batch(h, n_reads, ends[1] - ends[0], pd, q0, n_pos))) return rc;
+    if ((rc = reserve_batch(h, n_reads, ends[1] - ends[0], pd, q0, n_pos, h->stream))) return rc;
     pd.seq = (const unsigned char*)seq;
     pd.qual = (const unsigned char*)qual;
     pd.offsets = (const unsigned long long*)offsets;
@@ -867,7 +875,7 @@ int kmer_analysis_count(kma_handle* h, const char* seq, const char* qual, const 
     const u64 nb = offsets[r1] - offsets[r0];
     PackDesc pd;
     u64 q0, n_pos;
-    if ((rc = reserve_batch(h, r1 - r0, nb, pd, q0, n_pos))) return rc;
+    if ((rc = reserve_batch(h, r1 - r0, nb, pd, q0, n_pos, h->stream))) return rc;
     const int b = h->stage_next;
     h->stage_next ^= 1;
     KMA_CUDA(cudaStreamWaitEvent(h->copy_stream, h->consumed[b], 0));
@@ -1096,7 +1104,7 @@ int kmer_analysis_count_batch(kma_handle* const* hs, const kma_reads* reads, uin
     if (reads[i].n_reads == 0) continue;
     PackDesc pd;
     u64 q0, n_pos;
-    int rc = reserve_batch(h, reads[i].n_reads, reads[i].n_bases, pd, q0, n_pos);
+    int rc = reserve_batch(h, reads[i].n_reads, reads[i].n_bases, pd, q0, n_pos, h0->stream);
     if (rc) return rc;
     pd.seq = (const unsigned char*)reads[i].seq;
     pd.qual = (const unsigned char*)reads[i].qual;
