@@ -315,7 +315,7 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.current_stream(dev)
     if args.autotune:
         autotune_workload(args, rs, seq, qual, offs, ws, rank)
-    hkw, tuning_source = handle_kwargs(rs, n_parts=ws, part=rank, **args.tuning)
+    hkw, tuning_source = handle_kwargs(rs, n_parts=ws, part=rank, tuned=args.tuned, **args.tuning)
     from paper_1705_11147_gb300 import make_params
     prm = make_params(**hkw)
     from paper_1705_11147_gb300 import plan as _plan
@@ -575,7 +575,7 @@ def run_batched(args, ws, rank, local):
               torch.from_numpy(rs.offsets.astype(np.int64)).to(dev)) for rs in sets]
 
     def params(rs):
-        return make_handle_params(rs, **args.tuning)
+        return make_handle_params(rs, tuned=args.tuned, **args.tuning)
 
     handles = [KmerAnalysis(params(rs)) for rs in sets]
     g = BatchGraph(handles, reads)
@@ -675,7 +675,7 @@ def run_served(args, ws, rank, local):
         # results are reduced to their window counts as they complete (the records of all
         # jobs would not fit in host memory at the larger scales); digests are taken after
         # the timed region
-        with Server(max_batch=args.max_batch, workers=args.workers) as srv:
+        with Server(max_batch=args.max_batch, workers=args.workers, tuned=args.tuned) as srv:
             t0 = time.perf_counter()
             futs = [srv.submit(j) for j in jobs]
             windows = []
@@ -688,23 +688,23 @@ def run_served(args, ws, rank, local):
     saturate()  # warm-up (pools, module load)
     t_srv, win_srv, batches, phases = saturate()
     t0 = time.perf_counter()
-    win_plain = [int(r.valid_windows) for r in run_plain(jobs, keep=False)]
+    win_plain = [int(r.valid_windows) for r in run_plain(jobs, keep=False, tuned=args.tuned)]
     t_plain = time.perf_counter() - t0
     windows = sum(win_srv)
     assert win_srv == win_plain
     # every served job's records against its plain run, job by job (outside the timed region)
     n_check = min(len(jobs), args.check_jobs)
-    with Server(max_batch=args.max_batch, workers=args.workers) as srv:
+    with Server(max_batch=args.max_batch, workers=args.workers, tuned=args.tuned) as srv:
         futs = [srv.submit(j) for j in jobs[:n_check]]
         dig_srv = []
         for i in range(len(futs)):
             dig_srv.append(records_digest(futs[i].result()))
             futs[i] = None
-    dig_plain = [records_digest(r) for r in run_plain(jobs[:n_check], keep=True, lazy=True)]
+    dig_plain = [records_digest(r) for r in run_plain(jobs[:n_check], keep=True, lazy=True, tuned=args.tuned)]
     same = dig_srv == dig_plain
     # latency under Poisson arrivals (arrival times of the first jobs, in real time)
     n_lat = min(len(jobs), args.latency_jobs)
-    with Server(max_batch=args.max_batch, workers=args.workers) as srv:
+    with Server(max_batch=args.max_batch, workers=args.workers, tuned=args.tuned) as srv:
         start = time.perf_counter()
         futs = []
         for j in jobs[:n_lat]:
@@ -723,7 +723,7 @@ def run_served(args, ws, rank, local):
             "config": {"workload": "served_500", "jobs": len(jobs), "scale": args.scale,
                        "bases": int(sum(j.n_bases for j in jobs)), "valid_windows": windows,
                        "max_batch": args.max_batch, "workers": args.workers,
-                       "saturation": "all jobs released at t=0"},
+                       "tuned": bool(args.tuned), "saturation": "all jobs released at t=0"},
             "plain": {"value": round(plain_value, 3), "unit": UNIT, "seconds": round(t_plain, 3),
                       "path": "create -> count (host reads) -> finalize -> copy -> destroy, one job at a time"},
             "served_vs_plain": round(value / plain_value, 3), "batches": batches,
@@ -755,7 +755,7 @@ def run_satellite(args, ws, rank, local):
     t_est = time.perf_counter() - t0
 
     def timed(heavy):
-        with KmerAnalysis(make_handle_params(rs, heavy_hitters=heavy), stream=stream) as ka:
+        with KmerAnalysis(make_handle_params(rs, heavy_hitters=heavy, tuned=args.tuned), stream=stream) as ka:
             def step():
                 ka.reset()
                 ka.count(seq, qual, offs)
@@ -864,6 +864,8 @@ def main():
     ap.add_argument("--tune", action="append", default=[],
                     help="launch-shape override key=value (block_threads, windows_per_thread, "
                          "ctas_per_sm, warp_aggregate, slot_prefetch, load_factor)")
+    ap.add_argument("--no-tuned", dest="tuned", action="store_false",
+                    help="library defaults instead of the autotuner's choices for every handle")
     ap.add_argument("--autotune", action="store_true",
                     help="time the autotuner's candidates on the workload first and store the winner")
     ap.add_argument("--tune-out", default="",

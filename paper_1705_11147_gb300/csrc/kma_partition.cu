@@ -587,7 +587,6 @@ __device__ __forceinline__ void recount_round(const PartGeom& G, const RecountSt
     w.lo = kk.x;
     w.hi = kk.y;
   }
-  window_of(S.rinfo[e], w);
   const u64 h = key_hash(w.lo, w.hi);
   const unsigned p = part_of(h, G.P);
   // most first sightings are of k-mers seen once, which never reached the table: the key
@@ -596,6 +595,7 @@ __device__ __forceinline__ void recount_round(const PartGeom& G, const RecountSt
     const u64 m = keyfilter_mask(h, G.bloom_h);
     if ((__ldcg(G.keyfilter + (u64)p * G.Wk + keyfilter_index(h, G.Wk)) & m) != m) return;
   }
+  window_of(S.rinfo[e], w);  // extension outcomes: only for the sightings that may count
   Slot* sub = G.table + (u64)p * G.Sp;
   const u64 idx = table_index(h, G.Sp);
   const ulonglong2 kv = __ldcg(reinterpret_cast<const ulonglong2*>(sub + idx));
@@ -701,13 +701,19 @@ __global__ void __launch_bounds__(kKeyThreads) keyfilter_build_kernel(const __gr
     const u64 s0 = (c - p * chunks_per_part) * kKeyChunk;
     const Slot* sub = G.table + p * G.Sp;
     u64* kf = G.keyfilter + p * G.Wk;
+    // all of the thread's slot keys are loaded before the first atomic: the loads of a chunk
+    // are in flight together instead of one round trip each
+    constexpr int kPer = kKeyChunk / kKeyThreads;
+    ulonglong2 kv[kPer];
 #pragma unroll
-    for (int j = 0; j < kKeyChunk / kKeyThreads; ++j) {
+    for (int j = 0; j < kPer; ++j) {
       const u64 i = s0 + (u64)j * kKeyThreads + threadIdx.x;
-      if (i >= G.Sp) break;
-      const ulonglong2 kv = __ldcs(reinterpret_cast<const ulonglong2*>(sub + i));
-      if (kv.x == kEmpty && kv.y == kEmpty) continue;
-      const u64 h = key_hash(kv.x, kv.y);
+      kv[j] = i < G.Sp ? __ldcs(reinterpret_cast<const ulonglong2*>(sub + i)) : make_ulonglong2(kEmpty, kEmpty);
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      if (kv[j].x == kEmpty && kv[j].y == kEmpty) continue;
+      const u64 h = key_hash(kv[j].x, kv[j].y);
       atomicOr(kf + keyfilter_index(h, G.Wk), keyfilter_mask(h, G.bloom_h));
     }
   }

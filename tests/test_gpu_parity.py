@@ -830,6 +830,38 @@ def test_served_subset_vs_oracle(gpu):
         assert res.valid_windows == want.valid_windows
 
 
+@pytest.mark.slow
+def test_served_quarter_scale_vs_oracle(gpu):
+    """The served workload at the scale the served comparison runs (genomes log-U[1, 50] Mbp
+    x 0.25, the first 250 jobs): the largest of those 250 jobs and nine of the first jobs, with
+    three workers and the bench's per-job parameters, so that jobs above the host-count size
+    are counted from host memory through the library's staged copies. Every job equals the
+    oracle on 2 of 16 owner partitions (by the oracle's own hash); window counts whole."""
+    import bench
+    from paper_1705_11147_gb300.serve import Job, Server
+    specs = synth.served_specs(250, scale=0.25)
+    largest = max(range(len(specs)), key=lambda j: specs[j]["G"])
+    pick = sorted({largest} | set(range(9)))
+    jobs, sets = [], []
+    for i in pick:
+        rs = synth.sample_reads(specs[i])
+        p = dict(rs.meta["params"])
+        p.pop("bloom_fpr", None)
+        p.update(bench.workload_sizing(rs))
+        jobs.append(Job(rs.seq, rs.qual, rs.offsets, params=p, job_id=i))
+        sets.append(rs)
+    srv = Server(max_batch=8, workers=3)
+    assert max(j.n_bases for j in jobs) >= srv.host_count_bases  # the host-memory path runs
+    with srv:
+        got = [f.result(timeout=1800) for f in [srv.submit(j) for j in jobs]]
+    for i, (res, rs) in enumerate(zip(got, sets)):
+        k = rs.meta["params"]["k"]
+        parts = [(2 * i + d) % 16 for d in range(2)]
+        want = oracle.run_readset(rs, n_parts=16, parts=parts)
+        assert_same(_owner_subset(res, k, 16, parts), want, f"job {pick[i]}")
+        assert res.valid_windows == want.valid_windows
+
+
 # ------------------------------------------------------------------ multi-GPU owner shards
 
 @pytest.mark.parametrize("n_parts", [2, 3])
