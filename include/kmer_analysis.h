@@ -200,7 +200,8 @@ int kmer_analysis_query(kma_handle* h, const uint64_t* keys, uint64_t n, uint32_
                         uint32_t* ext, uint8_t* codes, int on_device);
 
 /* Empty the handle for a new read set with the same parameters, keeping its memory
- * (arena, Bloom filter and table are cleared on the stream). */
+ * (Bloom filter and table are cleared on the stream; the packed-read arena is rewritten by
+ * the next count calls). */
 int kmer_analysis_reset(kma_handle* h);
 
 /* Change the stream later calls enqueue on (the caller orders the two streams). */

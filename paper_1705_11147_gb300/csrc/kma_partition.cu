@@ -238,13 +238,15 @@ static_assert(sizeof(WarpStage<1, 2>) % 16 == 0 && sizeof(WarpStage<2, 2>) % 16 
 // [p_begin, p_end), tpb per bucket, then the tiles of the overflow area (if the launch covers
 // it). Tile numbers, bucket numbers and record counts within a bucket fit 32 bits (the host
 // checks each record batch). cb / cf: the bucket whose record count was loaded last.
+// tinv: 0, or tile_inverse(tpb), with which the bucket number is a multiply-high instead of a
+// division.
 template <int TILE>
 __device__ __forceinline__ unsigned rec_tile(const PartGeom& G, const PartRecords& R, unsigned tpb, unsigned nb,
-                                             unsigned t, u64& base, unsigned& cb, unsigned& cf) {
+                                             unsigned t, u64& base, unsigned& cb, unsigned& cf, u64 tinv) {
   unsigned f, lo;
   u64 b0;
   if (t < nb) {
-    const unsigned q = t / tpb;
+    const unsigned q = tinv ? (tpb == 1 ? t : (unsigned)__umul64hi((u64)t, tinv)) : t / tpb;
     const unsigned b = R.p_begin + q;
     if (b != cb) {
       const u64 x = R.fill[b];
@@ -274,12 +276,17 @@ __device__ __forceinline__ unsigned rec_tile(const PartGeom& G, const PartRecord
 // ahead so that its queue round trip is hidden.
 constexpr unsigned kQueueChunk = 8;
 
+// floor(t / d) = high word of t * (floor((2^64 - 1) / d) + 1) for every t < 2^32 and 2 <= d <
+// 2^32 (division by an invariant integer through a rounded-up reciprocal, Granlund and
+// Montgomery, PLDI 1994): the product's error t * e / 2^64, e <= 1, stays below 1 / d.
+__device__ __forceinline__ u64 tile_inverse(unsigned d) { return d > 1 ? ~0ull / d + 1 : 0ull; }
+
 // Lane 0: the next non-empty tile from t on (its first record in base, t moved past it),
 // moving through the warp's chunks; returns its record count, 0 when no tile is left.
 template <int TILE>
 __device__ __forceinline__ unsigned rec_next(const PartGeom& G, const PartRecords& R, unsigned tpb, unsigned nb,
                                              unsigned n_tiles, unsigned& t, unsigned& c_end, unsigned& c_next,
-                                             u64& base, unsigned& cb, unsigned& cf) {
+                                             u64& base, unsigned& cb, unsigned& cf, u64 tinv = 0) {
   while (true) {
     if (t >= c_end) {  // chunk done: take the one grabbed ahead, grab the following one
       t = c_next * kQueueChunk;
@@ -287,7 +294,7 @@ __device__ __forceinline__ unsigned rec_next(const PartGeom& G, const PartRecord
       c_next = atomicAdd(R.queue, 1u);
     }
     if (t >= n_tiles) return 0;
-    const unsigned n = rec_tile<TILE>(G, R, tpb, nb, t, base, cb, cf);
+    const unsigned n = rec_tile<TILE>(G, R, tpb, nb, t, base, cb, cf, tinv);
     ++t;
     if (n) return n;
   }
@@ -623,6 +630,7 @@ __global__ void __launch_bounds__(kPartThreads, 5) part_recount_kernel(const __g
   const u64 pol = policy_evict_first();
   unsigned phases = 0;
   unsigned head = 0, tail = 0;  // ring: entries [head, tail) are waiting (same in every lane)
+  const u64 tinv = tile_inverse(tpb);  // lane 0's tile walk: bucket numbers without a division
 
   unsigned t = 0, cb = ~0u, cf = 0, c_end = 0, c_next = 0;
   u64 base = 0;
@@ -631,7 +639,7 @@ __global__ void __launch_bounds__(kPartThreads, 5) part_recount_kernel(const __g
     mbar_init(smem_u32(&S.bar[0]), 1);
     mbar_init(smem_u32(&S.bar[1]), 1);
     c_next = atomicAdd(R.queue, 1u);
-    n = rec_next<kTile>(G, R, tpb, nb, n_tiles, t, c_end, c_next, base, cb, cf);
+    n = rec_next<kTile>(G, R, tpb, nb, n_tiles, t, c_end, c_next, base, cb, cf, tinv);
     if (n) rec_issue_raw<KW>(S.keys[0], S.info[0], smem_u32(&S.bar[0]), R, base, n, pol);
   }
   __syncwarp();
@@ -642,7 +650,7 @@ __global__ void __launch_bounds__(kPartThreads, 5) part_recount_kernel(const __g
     u64 nbase = 0;
     unsigned nn = 0;
     if (lane == 0) {
-      nn = rec_next<kTile>(G, R, tpb, nb, n_tiles, t, c_end, c_next, nbase, cb, cf);
+      nn = rec_next<kTile>(G, R, tpb, nb, n_tiles, t, c_end, c_next, nbase, cb, cf, tinv);
       if (nn) rec_issue_raw<KW>(S.keys[buf ^ 1], S.info[buf ^ 1], smem_u32(&S.bar[buf ^ 1]), R, nbase, nn, pol);
     }
     nn = __shfl_sync(0xffffffffu, nn, 0);
