@@ -230,12 +230,21 @@ class Server:
 
     # ------------------------------------------------------------------ statistics
     def latency_stats(self) -> dict:
+        """Latency (arrival -> results) of the finished jobs: percentiles, split into the wait for
+        a worker (arrival -> batch start) and the batch's service time, and p50 of the largest
+        quarter of the jobs (by bases) against the rest."""
         lat = np.array([j.t_done - j.arrival for j in self.done])
         if lat.size == 0:
             return {"jobs": 0}
-        return {"jobs": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
-                "batches": self.batches}
+        wait = np.array([j.t_start - j.arrival for j in self.done])
+        service = lat - wait
+        size = np.array([j.n_bases for j in self.done])
+        big = size >= np.percentile(size, 75)
+        ms = lambda a, q: float(np.percentile(a, q) * 1e3) if a.size else 0.0  # noqa: E731
+        return {"jobs": int(lat.size), "p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99),
+                "mean_ms": float(lat.mean() * 1e3), "batches": self.batches,
+                "p99_wait_ms": ms(wait, 99), "p99_service_ms": ms(service, 99),
+                "p50_ms_largest_quarter": ms(lat[big], 50), "p50_ms_rest": ms(lat[~big], 50)}
 
 
 def run_plain(jobs: list[Job], device: int = 0, keep: bool = True, lazy: bool = False, tuned: bool = True):
