@@ -867,7 +867,9 @@ def main():
     ap.add_argument("--no-tuned", dest="tuned", action="store_false",
                     help="library defaults instead of the autotuner's choices for every handle")
     ap.add_argument("--autotune", action="store_true",
-                    help="time the autotuner's candidates on the workload first and store the winner")
+                    help="time the autotuner's candidates on the workload first and store the winner "
+                         "(measure in a separate run: the timing that follows in the same process "
+                         "can be perturbed)")
     ap.add_argument("--tune-out", default="",
                     help="tuning table to write with --autotune (default: the user cache)")
     args = ap.parse_args()

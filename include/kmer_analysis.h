@@ -100,8 +100,8 @@ typedef struct {
                                  one GPU): the Bloom filter and table are split by a hash into
                                  P parts, windows are first written to per-part record buckets,
                                  and the buckets are counted part by part so one part's filter
-                                 and table stay in L2. 0: automatic (P > 1 when filter + table
-                                 exceed 256 MB, about 48 MB per part); 1: one table, windows
+                                 and table stay in L2. 0: automatic (P >= 2 when filter + table
+                                 exceed 32 MB, at most 64 MB per part); 1: one table, windows
                                  counted in place; P >= 2: that many parts (<= 4096 for
                                  k <= 32, <= 2048 for k > 32; more: KMA_EINVAL). Results
                                  do not depend on it. */

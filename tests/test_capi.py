@@ -142,8 +142,11 @@ def test_table_and_arena_sizing(lib):
 
 def test_partition_sizing(lib):
     from paper_1705_11147_gb300 import capi
+    tiny = _plan(k=31, max_bases=1_000_000, expected_distinct=100_000, expected_keys=50_000)
+    assert tiny.partitions == 1                       # filter + table below 32 MB: one table
     small = _plan(k=51, max_bases=30_000_000, expected_distinct=4_400_000, expected_keys=1_100_000)
-    assert small.partitions == 1                      # filter + table below 256 MB: one table
+    per_small = (small.bloom_words * 8 + small.table_slots * 64) / small.partitions
+    assert small.partitions >= 2 and per_small <= 64 * 2**20 * 1.01  # above 32 MB: at least two
     big = _plan(k=51, max_bases=6_000_000_000, expected_distinct=2_100_000_000,
                 expected_keys=300_000_000)
     per_part = (big.bloom_words * 8 + big.table_slots * 64) / big.partitions
