@@ -227,6 +227,9 @@ struct WarpStage {
   unsigned char list[kTile];              // recount: indices of the flagged records
   unsigned char dup[64];                  // equal keys among a round of 32 records: a lane per hash slot
   unsigned acc[32][10];                   // per group leader: occurrences by left / right outcome
+  unsigned walk[8];                       // lane 0's tile walk: t, c_end, c_next, cb, cf, kept
+                                          // here: as registers they took five in every lane
+                                          // and the Bloom pass spilled
   unsigned long long bar[2];
 };
 static_assert(sizeof(WarpStage<1, 2>) % 16 == 0 && sizeof(WarpStage<2, 2>) % 16 == 0 &&
@@ -345,10 +348,18 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
   unsigned phases = 0;  // bit b: parity to wait for on buffer b (same in every lane)
 
   // lane 0's walk over the queue's chunks
-  unsigned t = 0, cb = ~0u, cf = 0, c_end = 0, c_next = 0;
+  unsigned& t = S.walk[0];
+  unsigned& c_end = S.walk[1];
+  unsigned& c_next = S.walk[2];
+  unsigned& cb = S.walk[3];
+  unsigned& cf = S.walk[4];
   u64 base = 0;
   unsigned n = 0;
   if (lane == 0) {
+    t = 0;
+    cb = ~0u;
+    cf = 0;
+    c_end = 0;
     mbar_init(smem_u32(&S.bar[0]), 1);
     mbar_init(smem_u32(&S.bar[1]), 1);
     c_next = atomicAdd(R.queue, 1u);
@@ -576,6 +587,7 @@ struct RecountStage {
   u64 rkeys[kRing * KW];
   unsigned char info[2][kTile];
   unsigned char rinfo[kRing];
+  unsigned walk[8];  // lane 0's tile walk: t, c_end, c_next, cb, cf (not in every lane's registers)
   unsigned long long bar[2];
 };
 static_assert(sizeof(RecountStage<1>) % 16 == 0 && sizeof(RecountStage<2>) % 16 == 0,
@@ -616,7 +628,7 @@ __device__ __forceinline__ void recount_round(const PartGeom& G, const RecountSt
 }
 
 template <int KW>
-__global__ void __launch_bounds__(kPartThreads, 5) part_recount_kernel(const __grid_constant__ PartGeom G,
+__global__ void __launch_bounds__(kPartThreads, 6) part_recount_kernel(const __grid_constant__ PartGeom G,
                                                                     const __grid_constant__ PartRecords R) {
   constexpr int kTile = RecountStage<KW>::kTile;
   constexpr int kWarps = kPartThreads / 32;
@@ -632,10 +644,18 @@ __global__ void __launch_bounds__(kPartThreads, 5) part_recount_kernel(const __g
   unsigned head = 0, tail = 0;  // ring: entries [head, tail) are waiting (same in every lane)
   const u64 tinv = tile_inverse(tpb);  // lane 0's tile walk: bucket numbers without a division
 
-  unsigned t = 0, cb = ~0u, cf = 0, c_end = 0, c_next = 0;
+  unsigned& t = S.walk[0];
+  unsigned& c_end = S.walk[1];
+  unsigned& c_next = S.walk[2];
+  unsigned& cb = S.walk[3];
+  unsigned& cf = S.walk[4];
   u64 base = 0;
   unsigned n = 0;
   if (lane == 0) {
+    t = 0;
+    cb = ~0u;
+    cf = 0;
+    c_end = 0;
     mbar_init(smem_u32(&S.bar[0]), 1);
     mbar_init(smem_u32(&S.bar[1]), 1);
     c_next = atomicAdd(R.queue, 1u);
