@@ -224,7 +224,6 @@ struct WarpStage {
   static constexpr int kTile = 32 * RPT;  // a multiple of 16
   u64 keys[2][kTile * KW];
   unsigned char info[2][kTile];
-  unsigned char list[kTile];              // recount: indices of the flagged records
   unsigned char dup[64];                  // equal keys among a round of 32 records: a lane per hash slot
   unsigned acc[32][10];                   // per group leader: occurrences by left / right outcome
   unsigned walk[8];                       // lane 0's tile walk: t, c_end, c_next, cb, cf, kept
@@ -332,8 +331,9 @@ __device__ __forceinline__ void rec_issue_raw(u64* keys, unsigned char* info, un
 __device__ __forceinline__ u64 shfl0(u64 v) { return __shfl_sync(0xffffffffu, v, 0); }
 
 template <int KW, int RPT, unsigned MODE, bool GROUP>
-__global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount ? 5 : 4) : 2) part_pass_kernel(const __grid_constant__ PartGeom G,
-                                                                 const __grid_constant__ PartRecords R) {
+__global__ void __launch_bounds__(kPartThreads, RPT == 2 ? 4 : 2) part_pass_kernel(const __grid_constant__ PartGeom G,
+                                                                                  const __grid_constant__ PartRecords R) {
+  static_assert(MODE == kModeBloom || MODE == kModeCount, "the recount has its own kernel");
   constexpr int kTile = WarpStage<KW, RPT>::kTile;
   constexpr int kWarps = kPartThreads / 32;
   __shared__ __align__(128) WarpStage<KW, RPT> stage[kWarps];
@@ -394,23 +394,6 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
     const u64* sk = S.keys[buf];
     const unsigned char* si = S.info[buf];
 
-    // records of this tile the lanes work on: all of them, or (recount) the flagged ones,
-    // compacted so that every lane has work
-    unsigned nwork = n;
-    if (MODE == kModeRecount) {
-      unsigned below = 0;
-#pragma unroll
-      for (int j = 0; j < RPT; ++j) {
-        const unsigned i = j * 32 + lane;
-        const bool f = i < n && (si[i] & kInfoFirst);
-        const unsigned m = __ballot_sync(0xffffffffu, f);
-        if (f) S.list[below + __popc(m & ((1u << lane) - 1u))] = (unsigned char)i;
-        below += __popc(m);
-      }
-      nwork = below;
-      __syncwarp();
-    }
-
     Window w[RPT];
     u64 h[RPT];
     unsigned p[RPT], rec[RPT];
@@ -419,8 +402,8 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
       const unsigned k = j * 32 + lane;
-      act[j] = k < nwork;
-      rec[j] = MODE == kModeRecount ? (act[j] ? S.list[k] : 0u) : k;
+      act[j] = k < n;
+      rec[j] = k;
       h[j] = 0;
       p[j] = 0;
       if (act[j]) {
@@ -453,7 +436,7 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
       dup[j] = false;
       ldr[j] = lane;
     }
-    if (GROUP && MODE != kModeRecount) {
+    if (GROUP) {
 #pragma unroll
       for (int j = 0; j < RPT; ++j) {
         const unsigned slot = (unsigned)h[j] & 63u;
@@ -492,16 +475,6 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
         }
       }
     }
-    // recount: most first sightings are of k-mers seen once, which never reached the table;
-    // the key filter (every inserted key sets its bits) rules them out without a probe
-    if (MODE == kModeRecount && G.Wk) {
-#pragma unroll
-      for (int j = 0; j < RPT; ++j) {
-        if (!act[j]) continue;
-        const u64 m = keyfilter_mask(h[j], G.bloom_h);
-        act[j] = (__ldcg(G.keyfilter + (u64)p[j] * G.Wk + keyfilter_index(h[j], G.Wk)) & m) == m;
-      }
-    }
     // stage 3: first probe in the partition's sub-table (group leaders only)
     ulonglong2 kv[RPT];
     u64 idx[RPT];
@@ -509,7 +482,7 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
     for (int j = 0; j < RPT; ++j) {
       kv[j] = make_ulonglong2(0, 0);
       idx[j] = 0;
-      if (act[j] && (MODE == kModeRecount || !dup[j])) {
+      if (act[j] && !dup[j]) {
         idx[j] = table_index(h[j], G.Sp);
         kv[j] = __ldcg(reinterpret_cast<const ulonglong2*>(G.table + (u64)p[j] * G.Sp + idx[j]));
       }
@@ -519,19 +492,13 @@ __global__ void __launch_bounds__(kPartThreads, RPT == 2 ? (MODE == kModeRecount
     for (int j = 0; j < RPT; ++j) {
       Slot* s = nullptr;
       bool inserted = false;
-      if (act[j] && (MODE == kModeRecount || !dup[j])) {
+      if (act[j] && !dup[j]) {
         Slot* sub = G.table + (u64)p[j] * G.Sp;
-        if (MODE == kModeRecount) {
-          bool full;
-          s = resolve_find(sub, G.Sp, idx[j], kv[j], w[j].lo, w[j].hi, full);
-          if (full) atomicOr(&G.status->flags, kFlagFull);
-        } else {
-          s = resolve_insert(sub, G.Sp, idx[j], kv[j], w[j].lo, w[j].hi, inserted);
-          if (!s) atomicOr(&G.status->flags, kFlagFull);
-        }
+        s = resolve_insert(sub, G.Sp, idx[j], kv[j], w[j].lo, w[j].hi, inserted);
+        if (!s) atomicOr(&G.status->flags, kFlagFull);
       }
-      if (MODE != kModeRecount) acc_ins += __popc(__ballot_sync(0xffffffffu, inserted));
-      if (GROUP && MODE != kModeRecount && anydup) {
+      acc_ins += __popc(__ballot_sync(0xffffffffu, inserted));
+      if (GROUP && anydup) {
         // sum each group's outcomes in its leader's block, then the leader applies them
         unsigned* blk = S.acc[lane];
 #pragma unroll
