@@ -10,7 +10,9 @@ staged copies overlapping the packing, in one call that releases the interpreter
 finalized together (kmer_analysis_finalize_batch). While one
 worker's batch is on the GPU the other workers copy in and launch the next jobs, so work of
 jobs that arrive while others run overlaps on the device. A finished job's table can stay
-resident for queries (`keep_resident`) until the caller releases it.
+resident for queries (`keep_resident`) until the caller releases it. Each job's counting
+parameters take the autotuner's choices for its class (`tuned`, see autotune.apply), and
+`latency_stats()` splits latency into the wait for a worker and the batch's service time.
 
 All counting runs in the library's kernels; this module schedules, copies and bookkeeps.
 """
