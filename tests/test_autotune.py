@@ -99,3 +99,22 @@ def test_tune_on_gpu(tmp_path):
     # the choice reaches a handle through apply(): explicit keywords win
     kw, src = autotune.apply(dict(base), path=path, shipped=None)
     assert src == "cache" and kw == {**base, **entry["resolved"]}
+
+
+def test_bench_handles_take_the_tuning(tmp_path, monkeypatch):
+    """The bench's handle keywords come through apply(): an entry for the job's class in the
+    user cache is used (source "cache"), explicit keywords win, and --no-tuned bypasses it."""
+    import bench
+    from paper_1705_11147_gb300 import autotune, build
+    build.build()
+    rs = synth.workload("plain_1m", scale=0.05)
+    path = str(tmp_path / "tune.json")
+    monkeypatch.setenv("KMA_TUNE_CACHE", path)
+    gpu = autotune._gpu_name()
+    autotune.save_cache({autotune.cache_key(gpu, 31, rs.n_bases): {"params": {"load_factor": 0.6}}}, path)
+    kw, src = bench.handle_kwargs(rs)
+    assert src == "cache" and kw["load_factor"] == 0.6
+    kw, src = bench.handle_kwargs(rs, load_factor=0.7)
+    assert kw["load_factor"] == 0.7
+    kw, src = bench.handle_kwargs(rs, tuned=False)
+    assert src == "none" and "load_factor" not in kw
