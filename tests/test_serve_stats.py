@@ -24,3 +24,19 @@ def test_latency_split_and_size_classes():
     assert abs(st["p99_service_ms"] - 90.0) < 0.1
     assert abs(st["mean_ms"] - 55.0) < 1e-6
     assert Server.latency_stats(SimpleNamespace(done=[], batches=0)) == {"jobs": 0}
+
+
+def test_job_parameters_take_the_tuning(tmp_path, monkeypatch):
+    """A served job's counting parameters fill what the job leaves open from the autotuner's
+    entry for its class; tuned=False keeps the library's automatic choices."""
+    from paper_1705_11147_gb300 import autotune, build
+    from paper_1705_11147_gb300.serve import Job
+    build.build()
+    n = 40_000_000
+    job = Job(seq=np.zeros(0, np.uint8), qual=np.zeros(0, np.uint8),
+              offsets=np.array([0, n], dtype=np.uint64), params={"k": 51, "min_depth": 2})
+    path = str(tmp_path / "tune.json")
+    monkeypatch.setenv("KMA_TUNE_CACHE", path)
+    autotune.save_cache({autotune.cache_key(autotune._gpu_name(), 51, n): {"params": {"partitions": 6}}}, path)
+    assert job.kma_params(True).partitions == 6
+    assert job.kma_params(False).partitions == 0
